@@ -1,0 +1,512 @@
+// FP64 CPU oracle for the binary-fluid D3Q19 lattice-Boltzmann timestep.
+//
+// TEST INFRASTRUCTURE ONLY. Nothing in the product path may link, load or call
+// this file: only the tests, the smoke check and the CPU-baseline leg of the
+// benchmark do. It shares no code, header, table or helper with the CUDA
+// library; the two are independent statements of the same method.
+//
+// What it computes. The paper (Gray & Stratford, "A Lightweight Approach to
+// Performance Portability with targetDP", Sec. 2.1.1) names the kernels of one
+// Ludwig timestep -- "Collision", "Propagation", "Chemical stress" and
+// "Order Parameter Gradients" -- but prints none of their equations. The
+// binary-fluid instance computed here is the standard one those names stand
+// for:
+//   * the D3Q19 velocity set and weights (Qian, d'Humieres & Lallemand 1992);
+//   * BGK collision of f with the Guo-Zheng-Shi (2002) forcing term and the
+//     half-force velocity u = (j + F/2)/rho;
+//   * BGK collision of g towards an equilibrium whose zeroth, first and second
+//     moments are phi, phi*u and Gamma*mu*I + phi*u*u;
+//   * the symmetric phi^4 free energy: mu = A phi + B phi^3 - kappa lap(phi),
+//     lap the 7-point Laplacian, force F = -phi * grad(mu), grad the 2-point
+//     central difference;
+//   * propagation: f_i(x + c_i, t+1) = f*_i(x, t) on a periodic lattice.
+// One step is: moments -> phi stencil and mu -> force and velocity ->
+// collide f -> collide g -> propagate, all stencils on fields of the same
+// time level. The state between steps is the post-propagation
+// (pre-collision) pair f, g.
+//
+// Layout: site s = x + nx*(y + ny*z) (x fastest); distribution component i of
+// site s at [i*N + s]; vector fields (u, grad phi, F) as [a*N + s].
+// Arithmetic is plain double; the build passes -ffp-contract=off so that no
+// fused multiply-add changes the rounding of what is written here.
+//
+// The whole scheme is templated on the scalar type: with T = double it is the
+// oracle; with T = Dual (value + one directional derivative) the same source
+// is the tangent-linear model used to check the adjoint.
+//
+// Every function carries a pin in tests/test_oracle_pins.py; none is
+// "parity unpinned".
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// D3Q19 velocity set (Qian, d'Humieres & Lallemand 1992). Order: rest; the six
+// axis vectors +x,-x,+y,-y,+z,-z; then the twelve face diagonals in pairs
+// (v, -v). The opposite of an odd index i is i+1.
+const int kQ = 19;
+const int kCx[kQ] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+const int kCy[kQ] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+const int kCz[kQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+
+double weight(int i) {
+    if (i == 0) return 1.0 / 3.0;
+    if (i <= 6) return 1.0 / 18.0;
+    return 1.0 / 36.0;
+}
+
+// ---------------------------------------------------------------------------
+// Dual number: value and one directional derivative (forward-mode AD).
+struct Dual {
+    double v, d;
+    Dual() : v(0.0), d(0.0) {}
+    Dual(double value) : v(value), d(0.0) {}
+    Dual(double value, double deriv) : v(value), d(deriv) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) {
+    return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));
+}
+inline Dual operator+(Dual a, double b) { return Dual(a.v + b, a.d); }
+inline Dual operator+(double a, Dual b) { return Dual(a + b.v, b.d); }
+inline Dual operator-(Dual a, double b) { return Dual(a.v - b, a.d); }
+inline Dual operator-(double a, Dual b) { return Dual(a - b.v, -b.d); }
+inline Dual operator*(Dual a, double b) { return Dual(a.v * b, a.d * b); }
+inline Dual operator*(double a, Dual b) { return Dual(a * b.v, a * b.d); }
+inline Dual operator/(Dual a, double b) { return Dual(a.v / b, a.d / b); }
+inline Dual operator/(double a, Dual b) { return Dual(a / b.v, -a * b.d / (b.v * b.v)); }
+inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
+
+// ---------------------------------------------------------------------------
+template <class T>
+struct Params {
+    T A, B, kappa, Gamma, tau_f, tau_g, rho0;
+};
+
+struct Lattice {
+    int nx, ny, nz;
+    long n;
+    Lattice(int x, int y, int z) : nx(x), ny(y), nz(z), n((long)x * y * z) {}
+    long site(int x, int y, int z) const { return x + (long)nx * (y + (long)ny * z); }
+    // Site reached from (x,y,z) by the displacement (dx,dy,dz), periodic.
+    long shifted(int x, int y, int z, int dx, int dy, int dz) const {
+        int xs = ((x + dx) % nx + nx) % nx;
+        int ys = ((y + dy) % ny + ny) % ny;
+        int zs = ((z + dz) % nz + nz) % nz;
+        return site(xs, ys, zs);
+    }
+};
+
+// Equilibrium of f: w_i rho [1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u].
+template <class T>
+void feq_site(T rho, const T u[3], T out[kQ]) {
+    T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < kQ; ++i) {
+        T cu = kCx[i] * u[0] + kCy[i] * u[1] + kCz[i] * u[2];
+        out[i] = weight(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    }
+}
+
+// Equilibrium of g: second-order Hermite form with moments phi, phi u and
+// Gamma mu I + phi u u:
+//   w_i [phi + 3 phi c.u + 9/2 (Gamma mu - phi/3)(|c|^2 - 1)
+//        + 9/2 phi (c.u)^2 - 3/2 phi u.u].
+template <class T>
+void geq_site(T phi, const T u[3], T mu, T Gamma, T out[kQ]) {
+    T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    T pressure_dev = Gamma * mu - phi / 3.0;
+    for (int i = 0; i < kQ; ++i) {
+        T cu = kCx[i] * u[0] + kCy[i] * u[1] + kCz[i] * u[2];
+        int c2 = kCx[i] * kCx[i] + kCy[i] * kCy[i] + kCz[i] * kCz[i];
+        out[i] = weight(i) * (phi + 3.0 * phi * cu + 4.5 * pressure_dev * (double)(c2 - 1)
+                              + 4.5 * phi * cu * cu - 1.5 * phi * uu);
+    }
+}
+
+// Guo-Zheng-Shi (2002) source term, including its (1 - 1/(2 tau)) prefactor:
+//   (1 - 1/(2 tau)) w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F.
+template <class T>
+void guo_site(const T u[3], const T F[3], T tau, T out[kQ]) {
+    T pre = 1.0 - 1.0 / (2.0 * tau);
+    for (int i = 0; i < kQ; ++i) {
+        T cu = kCx[i] * u[0] + kCy[i] * u[1] + kCz[i] * u[2];
+        T ex = 3.0 * (kCx[i] - u[0]) + 9.0 * cu * kCx[i];
+        T ey = 3.0 * (kCy[i] - u[1]) + 9.0 * cu * kCy[i];
+        T ez = 3.0 * (kCz[i] - u[2]) + 9.0 * cu * kCz[i];
+        out[i] = pre * weight(i) * (ex * F[0] + ey * F[1] + ez * F[2]);
+    }
+}
+
+// 7-point Laplacian, periodic.
+template <class T>
+void laplacian(const Lattice& L, const T* phi, T* lap) {
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < L.nz; ++z)
+        for (int y = 0; y < L.ny; ++y)
+            for (int x = 0; x < L.nx; ++x) {
+                long s = L.site(x, y, z);
+                T sum = phi[L.shifted(x, y, z, 1, 0, 0)] + phi[L.shifted(x, y, z, -1, 0, 0)]
+                      + phi[L.shifted(x, y, z, 0, 1, 0)] + phi[L.shifted(x, y, z, 0, -1, 0)]
+                      + phi[L.shifted(x, y, z, 0, 0, 1)] + phi[L.shifted(x, y, z, 0, 0, -1)];
+                lap[s] = sum - 6.0 * phi[s];
+            }
+}
+
+// Central difference (h(x+e_a) - h(x-e_a))/2 for a = x, y, z, periodic.
+template <class T>
+void gradient(const Lattice& L, const T* h, T* grad) {
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < L.nz; ++z)
+        for (int y = 0; y < L.ny; ++y)
+            for (int x = 0; x < L.nx; ++x) {
+                long s = L.site(x, y, z);
+                grad[0 * L.n + s] = (h[L.shifted(x, y, z, 1, 0, 0)] - h[L.shifted(x, y, z, -1, 0, 0)]) / 2.0;
+                grad[1 * L.n + s] = (h[L.shifted(x, y, z, 0, 1, 0)] - h[L.shifted(x, y, z, 0, -1, 0)]) / 2.0;
+                grad[2 * L.n + s] = (h[L.shifted(x, y, z, 0, 0, 1)] - h[L.shifted(x, y, z, 0, 0, -1)]) / 2.0;
+            }
+}
+
+// mu = A phi + B phi^3 - kappa lap(phi).
+template <class T>
+void chemical_potential(const Lattice& L, const Params<T>& p, const T* phi, T* lap, T* mu) {
+    laplacian(L, phi, lap);
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < L.n; ++s)
+        mu[s] = p.A * phi[s] + p.B * phi[s] * phi[s] * phi[s] - p.kappa * lap[s];
+}
+
+// Propagation: out_i(x + c_i) = in_i(x) for every component i (a permutation).
+template <class T>
+void propagate(const Lattice& L, const T* in, T* out) {
+    for (int i = 0; i < kQ; ++i) {
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < L.nz; ++z)
+            for (int y = 0; y < L.ny; ++y)
+                for (int x = 0; x < L.nx; ++x)
+                    out[i * L.n + L.shifted(x, y, z, kCx[i], kCy[i], kCz[i])] =
+                        in[i * L.n + L.site(x, y, z)];
+    }
+}
+
+// Transpose of propagate: out_i(x) = in_i(x + c_i).
+template <class T>
+void propagate_reverse(const Lattice& L, const T* in, T* out) {
+    for (int i = 0; i < kQ; ++i) {
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < L.nz; ++z)
+            for (int y = 0; y < L.ny; ++y)
+                for (int x = 0; x < L.nx; ++x)
+                    out[i * L.n + L.site(x, y, z)] =
+                        in[i * L.n + L.shifted(x, y, z, kCx[i], kCy[i], kCz[i])];
+    }
+}
+
+// Macroscopic fields of a pre-collision state, in the order the step uses
+// them: rho, j, phi; lap(phi) and mu; grad(mu), F = -phi grad(mu),
+// u = (j + F/2)/rho.
+template <class T>
+struct Macro {
+    std::vector<T> rho, j, phi, lap, mu, gradmu, F, u;
+    explicit Macro(long n)
+        : rho(n), j(3 * n), phi(n), lap(n), mu(n), gradmu(3 * n), F(3 * n), u(3 * n) {}
+};
+
+template <class T>
+void macroscopic(const Lattice& L, const Params<T>& p, const T* f, const T* g, Macro<T>& m) {
+    const long n = L.n;
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < n; ++s) {
+        T rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, phi = 0.0;
+        for (int i = 0; i < kQ; ++i) {
+            T fi = f[i * n + s];
+            rho += fi;
+            jx += kCx[i] * fi;
+            jy += kCy[i] * fi;
+            jz += kCz[i] * fi;
+            phi += g[i * n + s];
+        }
+        m.rho[s] = rho;
+        m.j[0 * n + s] = jx;
+        m.j[1 * n + s] = jy;
+        m.j[2 * n + s] = jz;
+        m.phi[s] = phi;
+    }
+    chemical_potential(L, p, m.phi.data(), m.lap.data(), m.mu.data());
+    gradient(L, m.mu.data(), m.gradmu.data());
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < n; ++s)
+        for (int a = 0; a < 3; ++a) {
+            m.F[a * n + s] = -m.phi[s] * m.gradmu[a * n + s];
+            m.u[a * n + s] = (m.j[a * n + s] + m.F[a * n + s] / 2.0) / m.rho[s];
+        }
+}
+
+// Collision of both distributions at every site (in place on f, g).
+template <class T>
+void collide(const Lattice& L, const Params<T>& p, const Macro<T>& m, T* f, T* g) {
+    const long n = L.n;
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < n; ++s) {
+        T u[3] = {m.u[s], m.u[n + s], m.u[2 * n + s]};
+        T F[3] = {m.F[s], m.F[n + s], m.F[2 * n + s]};
+        T feq[kQ], src[kQ], geq[kQ];
+        feq_site(m.rho[s], u, feq);
+        guo_site(u, F, p.tau_f, src);
+        for (int i = 0; i < kQ; ++i) {
+            T fi = f[i * n + s];
+            f[i * n + s] = fi - (fi - feq[i]) / p.tau_f + src[i];
+        }
+        geq_site(m.phi[s], u, m.mu[s], p.Gamma, geq);
+        for (int i = 0; i < kQ; ++i) {
+            T gi = g[i * n + s];
+            g[i * n + s] = gi - (gi - geq[i]) / p.tau_g;
+        }
+    }
+}
+
+// One full timestep; tmp holds 19*N scalars.
+template <class T>
+void step(const Lattice& L, const Params<T>& p, T* f, T* g, T* tmp, Macro<T>& m) {
+    macroscopic(L, p, f, g, m);
+    collide(L, p, m, f, g);
+    const size_t bytes = sizeof(T) * kQ * L.n;
+    propagate(L, f, tmp);
+    std::memcpy(f, tmp, bytes);
+    propagate(L, g, tmp);
+    std::memcpy(g, tmp, bytes);
+}
+
+// Initial state: f = feq(rho, u); g = geq(phi, u, mu(phi)), no force.
+template <class T>
+void init_state(const Lattice& L, const Params<T>& p, const T* phi, const T* rho_in,
+                const T* u_in, T* f, T* g) {
+    const long n = L.n;
+    std::vector<T> lap(n), mu(n);
+    chemical_potential(L, p, phi, lap.data(), mu.data());
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < n; ++s) {
+        T rho = rho_in ? rho_in[s] : p.rho0;
+        T u[3] = {T(0.0), T(0.0), T(0.0)};
+        if (u_in) {
+            u[0] = u_in[s];
+            u[1] = u_in[n + s];
+            u[2] = u_in[2 * n + s];
+        }
+        T fe[kQ], ge[kQ];
+        feq_site(rho, u, fe);
+        geq_site(phi[s], u, mu[s], p.Gamma, ge);
+        for (int i = 0; i < kQ; ++i) {
+            f[i * n + s] = fe[i];
+            g[i * n + s] = ge[i];
+        }
+    }
+}
+
+Params<double> params_from(const double* prm) {
+    return Params<double>{prm[0], prm[1], prm[2], prm[3], prm[4], prm[5], prm[6]};
+}
+
+Params<Dual> dual_params_from(const double* prm, const double* dprm) {
+    Params<Dual> p;
+    p.A = Dual(prm[0], dprm[0]);
+    p.B = Dual(prm[1], dprm[1]);
+    p.kappa = Dual(prm[2], dprm[2]);
+    p.Gamma = Dual(prm[3], dprm[3]);
+    p.tau_f = Dual(prm[4], dprm[4]);
+    p.tau_g = Dual(prm[5], dprm[5]);
+    p.rho0 = Dual(prm[6], dprm[6]);
+    return p;
+}
+
+bool dims_ok(int nx, int ny, int nz) { return nx >= 1 && ny >= 1 && nz >= 1; }
+
+// Deterministic sum: per-plane partials, then planes in z order.
+double plane_ordered_sum(const Lattice& L, const double* a) {
+    std::vector<double> part(L.nz, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < L.nz; ++z) {
+        double acc = 0.0;
+        for (long s = (long)z * L.nx * L.ny; s < (long)(z + 1) * L.nx * L.ny; ++s) acc += a[s];
+        part[z] = acc;
+    }
+    double total = 0.0;
+    for (int z = 0; z < L.nz; ++z) total += part[z];
+    return total;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C interface (called from Python through ctypes by the tests only).
+// prm = {A, B, kappa, Gamma, tau_f, tau_g, rho0}. Return 0 on success, -1 on
+// bad arguments.
+extern "C" {
+
+int orc_version() { return 1; }
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads() {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_lattice(int* c, double* w) {
+    for (int i = 0; i < kQ; ++i) {
+        c[3 * i + 0] = kCx[i];
+        c[3 * i + 1] = kCy[i];
+        c[3 * i + 2] = kCz[i];
+        w[i] = weight(i);
+    }
+}
+
+void orc_feq(double rho, const double* u, double* out) { feq_site(rho, u, out); }
+
+void orc_geq(double phi, const double* u, double mu, double Gamma, double* out) {
+    geq_site(phi, u, mu, Gamma, out);
+}
+
+void orc_guo(const double* u, const double* F, double tau, double* out) {
+    guo_site(u, F, tau, out);
+}
+
+int orc_laplacian(int nx, int ny, int nz, const double* phi, double* lap) {
+    if (!dims_ok(nx, ny, nz) || !phi || !lap) return -1;
+    laplacian(Lattice(nx, ny, nz), phi, lap);
+    return 0;
+}
+
+int orc_gradient(int nx, int ny, int nz, const double* h, double* grad) {
+    if (!dims_ok(nx, ny, nz) || !h || !grad) return -1;
+    gradient(Lattice(nx, ny, nz), h, grad);
+    return 0;
+}
+
+int orc_propagate(int nx, int ny, int nz, int reverse, const double* in, double* out) {
+    if (!dims_ok(nx, ny, nz) || !in || !out || in == out) return -1;
+    Lattice L(nx, ny, nz);
+    if (reverse)
+        propagate_reverse(L, in, out);
+    else
+        propagate(L, in, out);
+    return 0;
+}
+
+int orc_init(int nx, int ny, int nz, const double* prm, const double* phi, const double* rho,
+             const double* u, double* f, double* g) {
+    if (!dims_ok(nx, ny, nz) || !prm || !phi || !f || !g) return -1;
+    init_state(Lattice(nx, ny, nz), params_from(prm), phi, rho, u, f, g);
+    return 0;
+}
+
+int orc_step(int nx, int ny, int nz, const double* prm, double* f, double* g, int nsteps) {
+    if (!dims_ok(nx, ny, nz) || !prm || !f || !g || nsteps < 0) return -1;
+    Lattice L(nx, ny, nz);
+    Params<double> p = params_from(prm);
+    std::vector<double> tmp(kQ * L.n);
+    Macro<double> m(L.n);
+    for (int t = 0; t < nsteps; ++t) step(L, p, f, g, tmp.data(), m);
+    return 0;
+}
+
+// Macroscopic output of a pre-collision state. Any output pointer may be
+// null. totals (if given) = {sum rho, sum phi, sum jx, sum jy, sum jz}.
+int orc_macros(int nx, int ny, int nz, const double* prm, const double* f, const double* g,
+               double* rho, double* u, double* phi, double* gradphi, double* mu, double* force,
+               double* totals) {
+    if (!dims_ok(nx, ny, nz) || !prm || !f || !g) return -1;
+    Lattice L(nx, ny, nz);
+    const long n = L.n;
+    Macro<double> m(n);
+    macroscopic(L, params_from(prm), f, g, m);
+    if (rho) std::memcpy(rho, m.rho.data(), sizeof(double) * n);
+    if (u) std::memcpy(u, m.u.data(), sizeof(double) * 3 * n);
+    if (phi) std::memcpy(phi, m.phi.data(), sizeof(double) * n);
+    if (mu) std::memcpy(mu, m.mu.data(), sizeof(double) * n);
+    if (force) std::memcpy(force, m.F.data(), sizeof(double) * 3 * n);
+    if (gradphi) gradient(L, m.phi.data(), gradphi);
+    if (totals) {
+        totals[0] = plane_ordered_sum(L, m.rho.data());
+        totals[1] = plane_ordered_sum(L, m.phi.data());
+        for (int a = 0; a < 3; ++a) totals[2 + a] = plane_ordered_sum(L, m.j.data() + a * n);
+    }
+    return 0;
+}
+
+// Tangent-linear model. Values in f, g; one direction in df, dg; parameter
+// direction dprm (same order as prm). Advances both by nsteps.
+int orc_step_tl(int nx, int ny, int nz, const double* prm, const double* dprm, double* f,
+                double* g, double* df, double* dg, int nsteps) {
+    if (!dims_ok(nx, ny, nz) || !prm || !dprm || !f || !g || !df || !dg || nsteps < 0) return -1;
+    Lattice L(nx, ny, nz);
+    const long nq = kQ * L.n;
+    Params<Dual> p = dual_params_from(prm, dprm);
+    std::vector<Dual> F(nq), G(nq), tmp(nq);
+    for (long k = 0; k < nq; ++k) {
+        F[k] = Dual(f[k], df[k]);
+        G[k] = Dual(g[k], dg[k]);
+    }
+    Macro<Dual> m(L.n);
+    for (int t = 0; t < nsteps; ++t) step(L, p, F.data(), G.data(), tmp.data(), m);
+    for (long k = 0; k < nq; ++k) {
+        f[k] = F[k].v;
+        df[k] = F[k].d;
+        g[k] = G[k].v;
+        dg[k] = G[k].d;
+    }
+    return 0;
+}
+
+// Loss L = sum_x (phi_T(x) - phi_target(x))^2 after init from phi0 (rho0,
+// u = 0) and nsteps steps, and its directional derivative along (dphi0,
+// dprm). dphi0 may be null (zero direction).
+int orc_loss_jvp(int nx, int ny, int nz, const double* prm, const double* dprm,
+                 const double* phi0, const double* dphi0, const double* phi_target, int nsteps,
+                 double* loss, double* dloss) {
+    if (!dims_ok(nx, ny, nz) || !prm || !dprm || !phi0 || !phi_target || nsteps < 0 || !loss ||
+        !dloss)
+        return -1;
+    Lattice L(nx, ny, nz);
+    const long n = L.n, nq = kQ * n;
+    Params<Dual> p = dual_params_from(prm, dprm);
+    std::vector<Dual> phi(n), F(nq), G(nq), tmp(nq);
+    for (long s = 0; s < n; ++s) phi[s] = Dual(phi0[s], dphi0 ? dphi0[s] : 0.0);
+    init_state<Dual>(L, p, phi.data(), nullptr, nullptr, F.data(), G.data());
+    Macro<Dual> m(n);
+    for (int t = 0; t < nsteps; ++t) step(L, p, F.data(), G.data(), tmp.data(), m);
+    double acc = 0.0, dacc = 0.0;
+    for (long s = 0; s < n; ++s) {
+        Dual ph = 0.0;
+        for (int i = 0; i < kQ; ++i) ph += G[i * n + s];
+        Dual r = ph - phi_target[s];
+        Dual r2 = r * r;
+        acc += r2.v;
+        dacc += r2.d;
+    }
+    *loss = acc;
+    *dloss = dacc;
+    return 0;
+}
+
+}  // extern "C"
