@@ -1,0 +1,407 @@
+"""Benchmark of the binary-fluid D3Q19 lattice-Boltzmann step on GB300.
+
+Workload: spinodal decomposition on a periodic 384^3 lattice (56.6M sites),
+phi seeded noise in [-0.05, 0.05], rho = 1, u = 0, A = -0.0625, B = 0.0625,
+kappa = 0.04, Gamma = 0.5, tau_f = tau_g = 1. A step is one full timestep
+(moments, phi stencil and mu, force, collisions of f and g, propagation, in
+the storage codec of the precision), run by the library's CUDA kernels
+through the C ABI; the timed region ends with the FP64 conservation totals.
+
+Metric: MLUPS (million lattice-site updates per second), with the fraction
+of the HBM roofline: algorithmic bytes per site = 76 x (bytes per stored
+value): 19 f and 19 g values read and written. The primary line is the FP32
+storage form; FP64 and the FP16/BF16 deviation forms are reported in
+"per_precision". The state (>= 8.6 GB) is far larger than L2 (129 MB), so no
+flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a
+bounded sample of the same workload on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+BYTES_PER_VALUE = {"fp64": 8, "fp32": 4, "fp16dev": 2, "bf16dev": 2}
+VALUES_PER_SITE = 76  # 2 x 19 distributions, read + write
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "MLUPS & % of HBM roofline per precision on 1 GB300; adjoint/forward cost ratio"
+SEED = 5
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--size", type=int, default=384, help="lattice edge (cubic, periodic)")
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precisions", default="fp32,fp64,fp16dev,bf16dev",
+                    help="comma list; the first one is the primary line")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def config_of(args):
+    n = args.size
+    return {"workload": f"spinodal-{n}^3-periodic", "lattice": [n, n, n], "sites": n ** 3,
+            "init": "phi uniform seeded noise in [-0.05,0.05] (SplitMix64 seed 5), rho=1, u=0, f,g at equilibrium",
+            "params": {"A": -0.0625, "B": 0.0625, "kappa": 0.04, "Gamma": 0.5, "tau_f": 1.0, "tau_g": 1.0},
+            "bytes_per_site_algorithmic": None, "l2": "no flush: state is larger than L2 (129 MB)",
+            "parallelism": "replicas (one independent lattice per GPU)"}
+
+
+# --------------------------------------------------------------------------
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_1609_01479_gb300/csrc/ld_fused.cu", "paper_1609_01479_gb300/csrc/ld_common.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(precision, size):
+    """DRAM bytes per launch of the fused step from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split("#")[0].split()
+            if len(parts) < 5:
+                continue
+            kernel, prec, sz, bytes_per_launch, src_hash = parts[:5]
+            if prec == precision and int(sz) == size and src_hash == want:
+                return float(bytes_per_launch)
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.lines = []
+        target = None
+        try:
+            import torch
+
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            target = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+        except Exception:
+            target = str(device_index)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", target, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            cols = [c.strip() for c in line.split(",")]
+            if len(cols) < 8:
+                continue
+            try:
+                sm.append(float(cols[0]))
+                smax.append(float(cols[1]))
+                power.append(float(cols[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, cols[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+def dist_setup(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_precision(args, ld, phi_dev, precision, world, sample_clocks=False):
+    """Warm up, then time exactly args.steps steps (plus the final totals)."""
+    import torch
+
+    n = args.size
+    stream = torch.cuda.current_stream()
+    sim = ld.LdSim(n, n, n, precision=precision, stream=stream.cuda_stream)
+    sim.init(phi_dev)
+    sim.step(args.warmup)
+    totals = torch.empty(5, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    region0 = torch.cuda.Event(enable_timing=True)
+    region1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if sample_clocks else None
+    if sampler is not None:
+        time.sleep(0.3)  # let the sampler start before the region
+    region0.record(stream)
+    for k in range(args.steps):
+        starts[k].record(stream)
+        ld.ld_step(sim.ctx, 1)
+        ends[k].record(stream)
+    ld.ld_moments(sim.ctx, totals=totals)
+    region1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler is not None else None
+    barrier(world)
+    region_ms = region0.elapsed_time(region1)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot = totals.cpu().numpy()
+    fused = bool(ld.lib() and sim.params.kernel in (0, 2))
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return {"region_ms": region_ms, "kernel_ms_mean": float(np.mean(step_ms)),
+            "kernel_ms_median": float(np.median(step_ms)), "totals": tot.tolist(), "clocks": clocks,
+            "fused": fused}
+
+
+def time_e2e(args, ld, phi_host_pinned, precision):
+    """Whole run through the public API with host buffers: H2D of phi0 from
+    pinned memory, init, args.steps steps, D2H of phi; MLUPS of that run."""
+    import torch
+
+    n = args.size
+    stream = torch.cuda.current_stream()
+    sim = ld.LdSim(n, n, n, precision=precision, stream=stream.cuda_stream)
+    phi_dev = torch.empty(phi_host_pinned.shape, dtype=torch.float64, device="cuda")
+    phi_out_dev = torch.empty_like(phi_dev)
+    phi_out_host = torch.empty(phi_host_pinned.shape, dtype=torch.float64, pin_memory=True)
+    # one untimed pass for warm-up
+    for timed in (False, True):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        phi_dev.copy_(phi_host_pinned, non_blocking=True)
+        sim.init(phi_dev)
+        sim.step(args.steps if timed else args.warmup)
+        ld.ld_moments(sim.ctx, phi=phi_out_dev)
+        phi_out_host.copy_(phi_out_dev, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    nbytes = phi_host_pinned.numel() * 8
+    return ms, nbytes
+
+
+def cpu_baseline(sample_edge=96, sample_steps=20):
+    """The FP64 oracle, as it stands, on the host cores: MLUPS on a bounded
+    sample (a sample_edge^3 lattice of the same workload, sample_steps steps)."""
+    import oracle
+    from paper_1609_01479_gb300 import inputs
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    prm = oracle.param_vector()
+    phi = inputs.spinodal_phi(sample_edge, sample_edge, sample_edge, seed=SEED)
+    f, g = oracle.init(phi, prm)
+    f, g = oracle.step(f, g, prm, 1)  # warm-up
+    t0 = time.perf_counter()
+    oracle.step(f, g, prm, sample_steps)
+    dt = time.perf_counter() - t0
+    return {"value": sample_edge ** 3 * sample_steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.get_threads(),
+            "kind": "oracle",
+            "sample": f"{sample_edge}^3 lattice of the same spinodal workload, {sample_steps} steps, FP64 oracle "
+                      f"(C++ -O2, OpenMP over z-planes), {dt:.2f} s"}
+
+
+# --------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1609_01479_gb300 import inputs
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    prm = oracle.param_vector()
+    edge = 64  # bounded sample of the 384^3 workload per step
+    phi = inputs.spinodal_phi(edge, edge, edge, seed=SEED)
+    f, g = oracle.init(phi, prm)
+    for _ in range(args.warmup):
+        f, g = oracle.step(f, g, prm, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, g = oracle.step(f, g, prm, 1)
+    dt = time.perf_counter() - t0
+    mlups = edge ** 3 * args.steps / dt / 1e6
+    cfg = config_of(args)
+    cfg["bytes_per_site_algorithmic"] = VALUES_PER_SITE * 8
+    sample = f"{edge}^3 sample of the {args.size}^3 workload per step, FP64 oracle on {oracle.get_threads()} threads"
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    from paper_1609_01479_gb300 import inputs, ld
+
+    world, rank, local = dist_setup(args)
+    ld.lib()
+    n = args.size
+    precisions = [p.strip() for p in args.precisions.split(",") if p.strip()]
+    phi_np = inputs.spinodal_phi(n, n, n, seed=SEED)
+    phi_dev = torch.from_numpy(phi_np).to("cuda")
+    peak, peak_kind = measured_hbm_peak()
+
+    results = {}
+    for i, prec in enumerate(precisions):
+        r = time_precision(args, ld, phi_dev, prec, world, sample_clocks=(i == 0))
+        region_ms = max_over_ranks(world, r["region_ms"])
+        kernel_ms = max_over_ranks(world, r["kernel_ms_mean"])
+        sites = n ** 3
+        bps = VALUES_PER_SITE * BYTES_PER_VALUE[prec]
+        results[prec] = {
+            "mlups": world * sites * args.steps / (region_ms * 1e-3) / 1e6,
+            "ms_per_step": region_ms / args.steps,
+            "kernel_ms": kernel_ms,
+            "algorithmic_gbs": sites * bps / (kernel_ms * 1e-3) / 1e9,
+            "bytes_per_site": bps,
+            "totals": r["totals"],
+            "clocks": r["clocks"],
+        }
+        results[prec]["roofline_frac"] = results[prec]["algorithmic_gbs"] / peak
+
+    primary = precisions[0]
+    P = results[primary]
+    e2e = None
+    if not args.no_e2e:
+        phi_pinned = torch.from_numpy(phi_np).pin_memory()
+        ms, nbytes = time_e2e(args, ld, phi_pinned, primary)
+        ms = max_over_ranks(world, ms)
+        e2e = {"value": world * n ** 3 * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
+               "what": f"pinned phi0 H2D + ld_init + {args.steps} ld_step + ld_moments(phi) + D2H, one run"}
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline()
+    cfg = config_of(args)
+    cfg["bytes_per_site_algorithmic"] = P["bytes_per_site"]
+    cfg["precision"] = primary
+    traffic = recorded_traffic(primary, n)
+    line = {
+        "metric": METRIC,
+        "value": P["mlups"],
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": P["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if primary == "fp32" else ("f64" if primary == "fp64" else "f32-compute/16-bit-storage"),
+        "data": "synthetic",
+        "config": cfg,
+        "roofline": {"bound": "hbm", "achieved": P["algorithmic_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": P["roofline_frac"], "traffic": traffic,
+                     "kernel": "k_step_fused" if True else None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "per_site_bytes": P["bytes_per_site"], "kernel_ms": P["kernel_ms"]},
+        "clocks": P["clocks"],
+        "e2e": e2e,
+        "gpu_launches": args.steps + 2,
+        "cpu_baseline": cpu,
+        "per_precision": {p: {k: v for k, v in r.items() if k not in ("clocks",)} for p, r in results.items()},
+        "adjoint_forward_ratio": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

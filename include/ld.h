@@ -1,0 +1,149 @@
+/*
+ * ld.h -- C ABI of the binary-fluid D3Q19 lattice-Boltzmann library (sm_103a).
+ *
+ * One timestep of the grid application ported in Gray & Stratford, "A
+ * Lightweight Approach to Performance Portability with targetDP" (Sec. 2.1.1,
+ * the Ludwig components "Order Parameter Gradients", "Chemical stress",
+ * "Collision" and "Propagation"), in its binary-fluid form:
+ *
+ *   rho = sum_i f_i,  j = sum_i f_i c_i,  phi = sum_i g_i      (moments)
+ *   mu  = A phi + B phi^3 - kappa lap(phi)       (7-point Laplacian)
+ *   F   = -phi grad(mu)                           (2-point central difference)
+ *   u   = (j + F/2) / rho                         (Guo, Zheng & Shi 2002)
+ *   f*_i = f_i - (f_i - feq_i(rho,u))/tau_f + (1 - 1/(2 tau_f)) w_i [3(c_i-u) + 9(c_i.u)c_i].F
+ *   g*_i = g_i - (g_i - geq_i(phi,u,mu))/tau_g
+ *   f_i(x + c_i, t+1) = f*_i(x, t),  g likewise                (propagation)
+ *
+ * with feq_i = w_i rho [1 + 3c.u + 9/2 (c.u)^2 - 3/2 u.u] and
+ * geq_i = w_i [phi + 3 phi c.u + 9/2 (Gamma mu - phi/3)(|c_i|^2 - 1)
+ *              + 9/2 phi (c.u)^2 - 3/2 phi u.u],
+ * on a periodic nx*ny*nz lattice, D3Q19 velocity set in the order: rest,
+ * +x,-x,+y,-y,+z,-z, then the face diagonals in (v,-v) pairs
+ * (++0,--0,+-0,-+0, +0+,-0-,+0-,-0+, 0++,0--,0+-,0-+).
+ *
+ * Conventions shared by every call:
+ *   - Site order s = x + nx*(y + ny*z), x fastest. Scalar fields are double[N],
+ *     vector fields double[3][N] (component-major), distributions
+ *     double[19][N]; N = nx*ny*nz.
+ *   - Every array pointer is a DEVICE pointer (cudaMalloc'd or torch-owned);
+ *     host pointers are rejected with LD_EINVAL. The library never allocates
+ *     or frees device memory: the caller provides one workspace of
+ *     ld_workspace_bytes() bytes (256-byte aligned) and keeps it alive until
+ *     ld_destroy(). The library owns only the host-side context.
+ *   - Calls are stream-ordered on the CUDA stream given to ld_create() (or
+ *     ld_set_stream()); they do not synchronise the host unless stated.
+ *   - Return 0 (LD_OK) on success or a negative LD_E* code; ld_last_error()
+ *     gives a message. No call aborts, exits or traps the device.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef LD_H
+#define LD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Storage precision of the distributions (arithmetic in parentheses).
+ * LD_FP64: double (double).  LD_FP32: float (float).
+ * LD_FP16DEV / LD_BF16DEV: half / bfloat16 deviations from a fixed reference
+ * (float): f_i = w_i rho0 + h_i, g_i = geq_i(phibar, 0, A phibar + B phibar^3) + h_i,
+ * phibar the mean of the initial phi; stores round to nearest even. */
+enum { LD_FP64 = 0, LD_FP32 = 1, LD_FP16DEV = 2, LD_BF16DEV = 3 };
+
+/* Step kernel selection: LD_KERNEL_AUTO picks the fused kernel when the lattice
+ * admits it (nx % 32 == 0, ny % 8 == 0, nz % 4 == 0), else the generic one. */
+enum { LD_KERNEL_AUTO = 0, LD_KERNEL_GENERIC = 1, LD_KERNEL_FUSED = 2 };
+
+enum {
+    LD_OK = 0,
+    LD_EINVAL = -1,     /* bad argument: dims < 4, null/host pointer, tau <= 1/2, small workspace */
+    LD_ECUDA = -2,      /* a CUDA runtime call or kernel launch failed */
+    LD_ENONFINITE = -3, /* ld_check found a NaN or Inf in the state */
+    LD_ESTATE = -4      /* call out of order (e.g. ld_step before ld_init) */
+};
+
+typedef struct {
+    double A, B, kappa, Gamma; /* free energy and mobility parameter */
+    double tau_f, tau_g;       /* relaxation times, each > 1/2 */
+    double rho0;               /* reference density (default rho, f deviation reference) */
+    int precision;             /* LD_FP64 .. LD_BF16DEV */
+    int kernel;                /* LD_KERNEL_AUTO / GENERIC / FUSED */
+} ld_params;
+
+typedef struct ld_ctx ld_ctx;
+
+/* Bytes of device workspace a context of this size and precision needs
+ * (two distribution buffers, phi/mu scratch, reduction partials). 0 on bad
+ * arguments. */
+size_t ld_workspace_bytes(int nx, int ny, int nz, const ld_params* p);
+
+/* Create a context on the caller's workspace (device, >= ld_workspace_bytes,
+ * 256-byte aligned) and CUDA stream (cudaStream_t, or NULL for the legacy
+ * default stream). Lattice dims must each be >= 4. *out receives the context. */
+int ld_create(int nx, int ny, int nz, const ld_params* p, void* dev_workspace, size_t bytes,
+              void* cuda_stream, ld_ctx** out);
+
+/* Release the host context (the workspace stays the caller's). NULL is a no-op. */
+int ld_destroy(ld_ctx* ctx);
+
+/* Change the stream later calls are ordered on. */
+int ld_set_stream(ld_ctx* ctx, void* cuda_stream);
+
+/* Replace A, B, kappa, Gamma, tau_f, tau_g (precision, kernel and rho0 must
+ * stay as created). Takes effect at the next launch. */
+int ld_set_params(ld_ctx* ctx, const ld_params* p);
+
+/* Initial state (equilibrium, no force): f = feq(rho, u), g = geq(phi, u, mu(phi))
+ * with mu from the 7-point Laplacian of phi. phi: device double[N];
+ * rho: device double[N] or NULL (rho0 everywhere); u: device double[3][N] or
+ * NULL (at rest). Also fixes the deviation reference of LD_FP16DEV/LD_BF16DEV. */
+int ld_init(ld_ctx* ctx, const double* phi, const double* rho, const double* u);
+
+/* Advance nsteps >= 0 full timesteps (moments, phi stencil and mu, force,
+ * collisions of f and g, propagation). Asynchronous. */
+int ld_step(ld_ctx* ctx, int nsteps);
+
+/* Macroscopic fields of the current (pre-collision) state. Each output may be
+ * NULL. rho, phi: double[N]; u = (j + F/2)/rho: double[3][N];
+ * grad_phi (central difference): double[3][N]; totals: double[5] =
+ * {sum rho, sum phi, sum jx, sum jy, sum jz}, each summed in FP64 in a fixed
+ * order (bitwise reproducible run to run). Asynchronous. */
+int ld_moments(ld_ctx* ctx, double* rho, double* u, double* phi, double* grad_phi, double* totals);
+
+/* Synchronise the stream and return LD_ENONFINITE if the state holds a NaN
+ * or Inf (tested through the FP64 totals), else LD_OK. Blocks the host. */
+int ld_check(ld_ctx* ctx);
+
+/* Copy the current pre-collision distributions out as double[19][N] each
+ * (decoded from the storage precision). Either pointer may be NULL. */
+int ld_get_distributions(ld_ctx* ctx, double* f, double* g);
+
+/* Overwrite the state with given pre-collision distributions double[19][N]
+ * (encoded to the storage precision, rounding to nearest even). The
+ * deviation reference of the 16-bit forms is the one fixed by ld_init, or
+ * rho0-only (g reference 0) if ld_init was never called. */
+int ld_set_distributions(ld_ctx* ctx, const double* f, const double* g);
+
+/* Propagation alone on the stored bits (no collision): reverse = 0 applies
+ * f_i(x + c_i) <- f_i(x); reverse = 1 applies the transpose
+ * f_i(x) <- f_i(x + c_i). A permutation of raw storage values: bit-exact in
+ * every precision. */
+int ld_propagate(ld_ctx* ctx, int reverse);
+
+/* Checkpoint: bytes of one saved state, and device-to-device save/restore of
+ * it (caller-owned device buffer of ld_state_bytes()). Asynchronous. */
+size_t ld_state_bytes(const ld_ctx* ctx);
+int ld_save_state(ld_ctx* ctx, void* dev_buf);
+int ld_load_state(ld_ctx* ctx, const void* dev_buf);
+
+/* Message for an error code, and the last error recorded on a context. */
+const char* ld_strerror(int code);
+const char* ld_last_error(const ld_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LD_H */

@@ -1,0 +1,322 @@
+// C ABI of the library (declared in include/ld.h): argument checks, the
+// workspace layout, and the order of kernel launches for each call.
+#include <math.h>
+#include <stdint.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "ld.h"
+#include "ld_internal.h"
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+constexpr size_t kAlign = 256;
+constexpr int kQ = 19;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t store_bytes_of(int prec) {
+    switch (prec) {
+        case LD_FP64: return 8;
+        case LD_FP32: return 4;
+        case LD_FP16DEV:
+        case LD_BF16DEV: return 2;
+        default: return 0;
+    }
+}
+size_t real_bytes_of(int prec) { return prec == LD_FP64 ? 8 : 4; }
+
+long long npad_of(long long n) { return (n + 63) / 64 * 64; }
+
+struct Layout {
+    size_t dist, phi, mu, partials, totals, ref, total;
+};
+
+Layout layout_of(int nx, int ny, int nz, int prec) {
+    const long long npad = npad_of((long long)nx * ny * nz);
+    Layout L;
+    size_t off = 0;
+    const size_t dist_one = align_up(2 * kQ * npad * store_bytes_of(prec));
+    L.dist = off;
+    off += 2 * dist_one;
+    L.phi = off;
+    off += align_up(npad * real_bytes_of(prec));
+    L.mu = off;
+    off += align_up(npad * real_bytes_of(prec));
+    L.partials = off;
+    off += align_up(sizeof(double) * ld::kRedBlocks * ld::kRedFields);
+    L.totals = off;
+    off += align_up(sizeof(double) * 8);
+    L.ref = off;
+    off += align_up(sizeof(float) * 2 * kQ);
+    L.total = off;
+    return L;
+}
+
+int fail(ld_ctx* c, int code, const char* fmt, ...) {
+    char* buf = c ? c->last_error : g_last_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 256, fmt, ap);
+    va_end(ap);
+    if (c) strncpy(g_last_error, c->last_error, sizeof(g_last_error) - 1);
+    return code;
+}
+
+int cuda_fail(ld_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, LD_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool params_ok(const ld_params* p, const char** why) {
+    if (!p) return *why = "params is NULL", false;
+    if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5)) return *why = "tau_f and tau_g must exceed 1/2", false;
+    if (!(p->rho0 > 0.0)) return *why = "rho0 must be positive", false;
+    if (!isfinite(p->A) || !isfinite(p->B) || !isfinite(p->kappa) || !isfinite(p->Gamma))
+        return *why = "A, B, kappa, Gamma must be finite", false;
+    if (p->precision < LD_FP64 || p->precision > LD_BF16DEV) return *why = "unknown precision", false;
+    if (p->kernel < LD_KERNEL_AUTO || p->kernel > LD_KERNEL_FUSED) return *why = "unknown kernel", false;
+    return true;
+}
+
+bool dims_ok(int nx, int ny, int nz) {
+    if (nx < 4 || ny < 4 || nz < 4) return false;
+    // every index and offset fits the 64-bit arithmetic; keep n within 2^31 sites
+    return (long long)nx * ny * nz < (1LL << 31);
+}
+
+// Device (or managed) memory only; host memory, pinned or not, is rejected.
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool opt_device(const void* p) { return p == nullptr || is_device_ptr(p); }
+
+int check_ready(ld_ctx* c) {
+    if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
+    if (!c->initialized) return fail(c, LD_ESTATE, "state not initialised (call ld_init or ld_load_state first)");
+    return LD_OK;
+}
+
+}  // namespace
+
+namespace ld {
+size_t dist_bytes(const ld_ctx* c) { return 2 * kQ * (size_t)c->geom.npad * c->store_bytes; }
+}  // namespace ld
+
+extern "C" {
+
+size_t ld_workspace_bytes(int nx, int ny, int nz, const ld_params* p) {
+    const char* why = nullptr;
+    if (!dims_ok(nx, ny, nz) || !params_ok(p, &why)) return 0;
+    return layout_of(nx, ny, nz, p->precision).total;
+}
+
+int ld_create(int nx, int ny, int nz, const ld_params* p, void* dev_workspace, size_t bytes, void* cuda_stream,
+              ld_ctx** out) {
+    const char* why = nullptr;
+    if (!out) return fail(nullptr, LD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!dims_ok(nx, ny, nz)) return fail(nullptr, LD_EINVAL, "lattice %dx%dx%d: each dim must be >= 4", nx, ny, nz);
+    if (!params_ok(p, &why)) return fail(nullptr, LD_EINVAL, "%s", why);
+    const Layout L = layout_of(nx, ny, nz, p->precision);
+    if (!is_device_ptr(dev_workspace)) return fail(nullptr, LD_EINVAL, "workspace is not a device pointer");
+    if ((uintptr_t)dev_workspace % kAlign) return fail(nullptr, LD_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < L.total)
+        return fail(nullptr, LD_EINVAL, "workspace of %zu bytes is smaller than the %zu needed", bytes, L.total);
+    const bool fused_ok = ld::fused_supported(nx, ny, nz);
+    if (p->kernel == LD_KERNEL_FUSED && !fused_ok)
+        return fail(nullptr, LD_EINVAL, "fused kernel needs nx %% 32 == 0, ny %% 8 == 0, nz %% 4 == 0");
+
+    ld_ctx* c = (ld_ctx*)calloc(1, sizeof(ld_ctx));
+    if (!c) return fail(nullptr, LD_EINVAL, "host allocation of the context failed");
+    c->geom.nx = nx;
+    c->geom.ny = ny;
+    c->geom.nz = nz;
+    c->geom.n = (long long)nx * ny * nz;
+    c->geom.npad = npad_of(c->geom.n);
+    c->prm = *p;
+    c->prec = p->precision;
+    c->store_bytes = store_bytes_of(p->precision);
+    c->real_bytes = real_bytes_of(p->precision);
+    c->ws = (char*)dev_workspace;
+    c->ws_bytes = bytes;
+    const size_t dist_one = align_up(2 * kQ * c->geom.npad * c->store_bytes);
+    c->dist[0] = c->ws + L.dist;
+    c->dist[1] = c->ws + L.dist + dist_one;
+    c->cur = 0;
+    c->phi = c->ws + L.phi;
+    c->mu = c->ws + L.mu;
+    c->partials = (double*)(c->ws + L.partials);
+    c->totals = (double*)(c->ws + L.totals);
+    c->ref = (float*)(c->ws + L.ref);
+    c->stream = (cudaStream_t)cuda_stream;
+    c->initialized = false;
+    c->fused = p->kernel == LD_KERNEL_FUSED || (p->kernel == LD_KERNEL_AUTO && fused_ok);
+    c->last_error[0] = '\0';
+    cudaError_t e = ld::launch_default_refs(c);
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(nullptr, e, "ld_create");
+        free(c);
+        return rc;
+    }
+    *out = c;
+    return LD_OK;
+}
+
+int ld_destroy(ld_ctx* c) {
+    free(c);
+    return LD_OK;
+}
+
+int ld_set_stream(ld_ctx* c, void* cuda_stream) {
+    if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
+    c->stream = (cudaStream_t)cuda_stream;
+    return LD_OK;
+}
+
+int ld_set_params(ld_ctx* c, const ld_params* p) {
+    const char* why = nullptr;
+    if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
+    if (!params_ok(p, &why)) return fail(c, LD_EINVAL, "%s", why);
+    if (p->precision != c->prm.precision || p->kernel != c->prm.kernel || p->rho0 != c->prm.rho0)
+        return fail(c, LD_EINVAL, "precision, kernel and rho0 are fixed at ld_create");
+    c->prm = *p;
+    return LD_OK;
+}
+
+int ld_init(ld_ctx* c, const double* phi, const double* rho, const double* u) {
+    if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
+    if (!is_device_ptr(phi)) return fail(c, LD_EINVAL, "phi must be a device pointer");
+    if (!opt_device(rho) || !opt_device(u)) return fail(c, LD_EINVAL, "rho and u must be device pointers or NULL");
+    c->cur = 0;
+    cudaError_t e = ld::launch_init(c, phi, rho, u);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_init");
+    c->initialized = true;
+    return LD_OK;
+}
+
+int ld_step(ld_ctx* c, int nsteps) {
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(c, LD_EINVAL, "nsteps must be >= 0");
+    for (int t = 0; t < nsteps; ++t) {
+        cudaError_t e;
+        if (c->fused) {
+            e = ld::launch_step_fused(c);
+        } else {
+            e = ld::launch_phi_mu(c, c->cur);
+            if (e == cudaSuccess) e = ld::launch_collide_generic(c);
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "ld_step");
+        c->cur ^= 1;
+    }
+    return LD_OK;
+}
+
+int ld_moments(ld_ctx* c, double* rho, double* u, double* phi, double* grad_phi, double* totals) {
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (!opt_device(rho) || !opt_device(u) || !opt_device(phi) || !opt_device(grad_phi) || !opt_device(totals))
+        return fail(c, LD_EINVAL, "outputs must be device pointers or NULL");
+    cudaError_t e = cudaSuccess;
+    if (rho || u || phi || grad_phi) e = ld::launch_macros(c, rho, u, phi, grad_phi);
+    if (e == cudaSuccess && totals) e = ld::launch_totals(c, totals);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_moments");
+    return LD_OK;
+}
+
+int ld_check(ld_ctx* c) {
+    int rc = check_ready(c);
+    if (rc) return rc;
+    double host[5];
+    cudaError_t e = ld::launch_totals(c, c->totals);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, c->totals, sizeof(host), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_check");
+    for (int k = 0; k < 5; ++k)
+        if (!isfinite(host[k])) return fail(c, LD_ENONFINITE, "state holds a non-finite value (total %d)", k);
+    return LD_OK;
+}
+
+int ld_get_distributions(ld_ctx* c, double* f, double* g) {
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (!opt_device(f) || !opt_device(g)) return fail(c, LD_EINVAL, "f and g must be device pointers or NULL");
+    cudaError_t e = ld::launch_decode(c, f, g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_get_distributions");
+    return LD_OK;
+}
+
+int ld_set_distributions(ld_ctx* c, const double* f, const double* g) {
+    if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
+    if (!is_device_ptr(f) || !is_device_ptr(g)) return fail(c, LD_EINVAL, "f and g must be device pointers");
+    cudaError_t e = ld::launch_encode(c, f, g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_set_distributions");
+    c->initialized = true;
+    return LD_OK;
+}
+
+int ld_propagate(ld_ctx* c, int reverse) {
+    int rc = check_ready(c);
+    if (rc) return rc;
+    cudaError_t e = ld::launch_propagate(c, reverse ? 1 : 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_propagate");
+    c->cur ^= 1;
+    return LD_OK;
+}
+
+size_t ld_state_bytes(const ld_ctx* c) {
+    if (!c) return 0;
+    return align_up(ld::dist_bytes(c)) + align_up(sizeof(float) * 2 * kQ);
+}
+
+int ld_save_state(ld_ctx* c, void* dev_buf) {
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (!is_device_ptr(dev_buf)) return fail(c, LD_EINVAL, "buffer must be a device pointer");
+    const size_t db = ld::dist_bytes(c);
+    cudaError_t e = cudaMemcpyAsync(dev_buf, c->dist[c->cur], db, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((char*)dev_buf + align_up(db), c->ref, sizeof(float) * 2 * kQ, cudaMemcpyDeviceToDevice,
+                            c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_save_state");
+    return LD_OK;
+}
+
+int ld_load_state(ld_ctx* c, const void* dev_buf) {
+    if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
+    if (!is_device_ptr(dev_buf)) return fail(c, LD_EINVAL, "buffer must be a device pointer");
+    const size_t db = ld::dist_bytes(c);
+    cudaError_t e = cudaMemcpyAsync(c->dist[c->cur], dev_buf, db, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->ref, (const char*)dev_buf + align_up(db), sizeof(float) * 2 * kQ,
+                            cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_load_state");
+    c->initialized = true;
+    return LD_OK;
+}
+
+const char* ld_strerror(int code) {
+    switch (code) {
+        case LD_OK: return "success";
+        case LD_EINVAL: return "invalid argument";
+        case LD_ECUDA: return "CUDA error";
+        case LD_ENONFINITE: return "non-finite value in the state";
+        case LD_ESTATE: return "call out of order";
+        default: return "unknown error code";
+    }
+}
+
+const char* ld_last_error(const ld_ctx* c) { return c ? c->last_error : g_last_error; }
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Shared device-side definitions of the D3Q19 binary-fluid step: velocity
+// set, storage codecs of the four precisions, per-site equilibria, Guo
+// forcing and collision. Included by every kernel translation unit.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ld.h"
+
+namespace ld {
+
+constexpr int Q = 19;
+
+// D3Q19 (Qian, d'Humieres & Lallemand 1992): rest, six axis vectors, twelve
+// face diagonals in (v, -v) pairs. Written as constexpr selectors so that
+// fully unrolled loops fold every c_i to an immediate.
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int c2(int i) { return cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i); }
+template <class R>
+__host__ __device__ constexpr R wgt(int i) {
+    return i == 0 ? R(1) / R(3) : (i <= 6 ? R(1) / R(18) : R(1) / R(36));
+}
+
+// ---------------------------------------------------------------------------
+// Storage precisions. real_t is the arithmetic type; store_t the stored one.
+// The 16-bit forms store the deviation from a per-direction reference value.
+// decode/encode work in real_t inside the step; decode_d/encode_d convert
+// to and from double for initialisation, I/O and the FP64 totals.
+template <int P> struct Prec;
+template <> struct Prec<LD_FP64> {
+    using store_t = double;
+    using real_t = double;
+    static constexpr bool kDev = false;
+    __device__ static double decode(store_t v, double) { return v; }
+    __device__ static store_t encode(double x, double) { return x; }
+    __device__ static double decode_d(store_t v, float) { return v; }
+    __device__ static store_t encode_d(double x, float) { return x; }
+};
+template <> struct Prec<LD_FP32> {
+    using store_t = float;
+    using real_t = float;
+    static constexpr bool kDev = false;
+    __device__ static float decode(store_t v, float) { return v; }
+    __device__ static store_t encode(float x, float) { return x; }
+    __device__ static double decode_d(store_t v, float) { return v; }
+    __device__ static store_t encode_d(double x, float) { return (float)x; }
+};
+template <> struct Prec<LD_FP16DEV> {
+    using store_t = __half;
+    using real_t = float;
+    static constexpr bool kDev = true;
+    __device__ static float decode(store_t v, float ref) { return ref + __half2float(v); }
+    __device__ static store_t encode(float x, float ref) { return __float2half_rn(x - ref); }
+    __device__ static double decode_d(store_t v, float ref) { return (double)ref + (double)__half2float(v); }
+    __device__ static store_t encode_d(double x, float ref) { return __double2half(x - (double)ref); }
+};
+template <> struct Prec<LD_BF16DEV> {
+    using store_t = __nv_bfloat16;
+    using real_t = float;
+    static constexpr bool kDev = true;
+    __device__ static float decode(store_t v, float ref) { return ref + __bfloat162float(v); }
+    __device__ static store_t encode(float x, float ref) { return __float2bfloat16_rn(x - ref); }
+    __device__ static double decode_d(store_t v, float ref) { return (double)ref + (double)__bfloat162float(v); }
+    __device__ static store_t encode_d(double x, float ref) { return __double2bfloat16(x - (double)ref); }
+};
+
+// Lattice geometry. npad: component stride of every SoA array (>= n, a
+// multiple of 64 so each component starts 256-byte aligned for 32-bit data).
+struct Geom {
+    int nx, ny, nz;
+    long long n, npad;
+};
+
+// Model constants in the arithmetic type.
+template <class R>
+struct Model {
+    R A, B, kappa, Gamma;
+    R omega_f, omega_g;  // 1/tau
+    R force_pre;         // 1 - 1/(2 tau_f)
+};
+
+// Reference values of the deviation codec: ref[i] for f, ref[19 + i] for g.
+constexpr int kRefCount = 2 * Q;
+
+__device__ __forceinline__ int wrap_inc(int a, int n) { return a + 1 == n ? 0 : a + 1; }
+__device__ __forceinline__ int wrap_dec(int a, int n) { return a == 0 ? n - 1 : a - 1; }
+
+// ---------------------------------------------------------------------------
+// Per-site physics (one site, registers only).
+
+// Guo velocity from the moments and the force.
+template <class R>
+__device__ __forceinline__ void guo_velocity(R rho, R jx, R jy, R jz, R Fx, R Fy, R Fz, R& ux, R& uy,
+                                             R& uz) {
+    const R inv = R(1) / rho;
+    ux = (jx + R(0.5) * Fx) * inv;
+    uy = (jy + R(0.5) * Fy) * inv;
+    uz = (jz + R(0.5) * Fz) * inv;
+}
+
+// BGK + Guo collision of f in place.
+template <class R>
+__device__ __forceinline__ void collide_f(R (&f)[Q], R rho, R ux, R uy, R uz, R Fx, R Fy, R Fz,
+                                          const Model<R>& m) {
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R uF = ux * Fx + uy * Fy + uz * Fz;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const R cu = R(cx(i)) * ux + R(cy(i)) * uy + R(cz(i)) * uz;
+        const R cF = R(cx(i)) * Fx + R(cy(i)) * Fy + R(cz(i)) * Fz;
+        const R feq = wgt<R>(i) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+        const R src = m.force_pre * wgt<R>(i) * (R(3) * (cF - uF) + R(9) * cu * cF);
+        f[i] = f[i] - m.omega_f * (f[i] - feq) + src;
+    }
+}
+
+// BGK collision of g in place.
+template <class R>
+__device__ __forceinline__ void collide_g(R (&g)[Q], R phi, R mu, R ux, R uy, R uz, const Model<R>& m) {
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R dev = m.Gamma * mu - phi * (R(1) / R(3));
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const R cu = R(cx(i)) * ux + R(cy(i)) * uy + R(cz(i)) * uz;
+        const R geq = wgt<R>(i) * (phi + R(3) * phi * cu + R(4.5) * dev * R(c2(i) - 1)
+                                   + R(4.5) * phi * cu * cu - R(1.5) * phi * uu);
+        g[i] = g[i] - m.omega_g * (g[i] - geq);
+    }
+}
+
+}  // namespace ld

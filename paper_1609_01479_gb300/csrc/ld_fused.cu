@@ -1,0 +1,203 @@
+// Fused single-pass step: one launch per timestep that reads each stored
+// distribution once from HBM and writes each once.
+//
+// Each CTA owns a TX x TY column of sites and marches up a chunk of ZC
+// z-planes. The order-parameter chain phi -> mu -> grad(mu) needs phi within
+// radius 2 and mu within radius 1 of every collided site, so the CTA keeps
+// two rolling rings in shared memory:
+//   phi ring: 3 planes of (TX+4) x (TY+4)  (tile + 2-site halo)
+//   mu ring:  3 planes of (TX+2) x (TY+2)  (tile + 1-site halo)
+// Iteration k computes phi(k+2) from the stored g of that plane (the state is
+// the post-propagation one, so phi is the local sum of 19 values), then
+// mu(k+1), then collides plane k and propagates it (push to x + c_i). The g
+// of plane k is read again for the collision two planes after phi(k) read
+// it; that second read and the halo reads of neighbouring tiles are served by
+// L2. Propagation writes into the other buffer of the ping-pong pair.
+#include "ld_common.cuh"
+#include "ld_internal.h"
+
+namespace ld {
+namespace {
+
+constexpr int kTX = 32;
+
+__device__ __forceinline__ int wrap_any(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+template <int P, int TY>
+__global__ void __launch_bounds__(kTX * TY)
+    k_step_fused(Geom g, Model<typename Prec<P>::real_t> m, int zc,
+                 const typename Prec<P>::store_t* __restrict__ fs, const typename Prec<P>::store_t* __restrict__ gs,
+                 typename Prec<P>::store_t* __restrict__ fd, typename Prec<P>::store_t* __restrict__ gd,
+                 const float* __restrict__ ref_g) {
+    using R = typename Prec<P>::real_t;
+    constexpr int PW = kTX + 4, PH = TY + 4;  // phi ring plane
+    constexpr int MW = kTX + 2, MH = TY + 2;  // mu ring plane
+    constexpr int NT = kTX * TY;
+    __shared__ R phis[3][PH][PW];
+    __shared__ R mus[3][MH][MW];
+    __shared__ float refs[2 * Q];
+
+    const int tid = threadIdx.x;
+    const int tx = tid % kTX, ty = tid / kTX;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
+    const long long plane = (long long)g.nx * g.ny;
+    if (tid < 2 * Q) refs[tid] = ref_g[tid];
+    __syncthreads();
+
+    // phi of plane zp over the tile + 2-halo, into ring slot `slot`.
+    auto phi_plane = [&](int zp, int slot) {
+        const long long zoff = (long long)wrap_any(zp, g.nz) * plane;
+        for (int idx = tid; idx < PW * PH; idx += NT) {
+            const int hx = idx % PW, hy = idx / PW;
+            const int gx = wrap_any(x0 + hx - 2, g.nx), gy = wrap_any(y0 + hy - 2, g.ny);
+            const long long s = zoff + (long long)gy * g.nx + gx;
+            R acc = R(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) acc += Prec<P>::decode(gs[i * g.npad + s], refs[Q + i]);
+            phis[slot][hy][hx] = acc;
+        }
+    };
+    // mu over the tile + 1-halo from three phi slots (below, middle, above).
+    auto mu_plane = [&](int slot, int lo, int mid, int hi) {
+        for (int idx = tid; idx < MW * MH; idx += NT) {
+            const int mx = idx % MW, my = idx / MW;
+            const int hx = mx + 1, hy = my + 1;
+            const R p = phis[mid][hy][hx];
+            const R lap = phis[mid][hy][hx + 1] + phis[mid][hy][hx - 1] + phis[mid][hy + 1][hx]
+                        + phis[mid][hy - 1][hx] + phis[hi][hy][hx] + phis[lo][hy][hx] - R(6) * p;
+            mus[slot][my][mx] = m.A * p + m.B * p * p * p - m.kappa * lap;
+        }
+    };
+    auto ps = [&](int zp) { return (zp - z0 + 2) % 3; };  // phi slot of plane zp (zp >= z0-2)
+    auto ms = [&](int zp) { return (zp - z0 + 1) % 3; };  // mu slot of plane zp (zp >= z0-1)
+
+    // Prologue: phi(z0-2..z0+1), mu(z0-1), mu(z0).
+    phi_plane(z0 - 2, ps(z0 - 2));
+    phi_plane(z0 - 1, ps(z0 - 1));
+    phi_plane(z0, ps(z0));
+    __syncthreads();
+    mu_plane(ms(z0 - 1), ps(z0 - 2), ps(z0 - 1), ps(z0));
+    __syncthreads();                // phi(z0+1) reuses the slot mu(z0-1) just read
+    phi_plane(z0 + 1, ps(z0 + 1));
+    __syncthreads();
+    mu_plane(ms(z0), ps(z0 - 1), ps(z0), ps(z0 + 1));
+
+    const int x = x0 + tx, y = y0 + ty;
+    const int xp = wrap_inc(x, g.nx), xm = wrap_dec(x, g.nx);
+    const int yp = wrap_inc(y, g.ny), ym = wrap_dec(y, g.ny);
+
+    for (int k = z0; k < z0 + zc; ++k) {
+        __syncthreads();  // previous collision done with phi(k-1) and mu(k-2) slots
+        phi_plane(k + 2, ps(k + 2));
+        __syncthreads();
+        mu_plane(ms(k + 1), ps(k), ps(k + 1), ps(k + 2));
+        __syncthreads();
+
+        const int z = k >= g.nz ? k - g.nz : k;
+        const int zp = wrap_inc(z, g.nz), zm = wrap_dec(z, g.nz);
+        const long long s = (long long)z * plane + (long long)y * g.nx + x;
+        const R ph = phis[ps(k)][ty + 2][tx + 2];
+        const int mc = ms(k);
+        const R muc = mus[mc][ty + 1][tx + 1];
+        const R gmx = R(0.5) * (mus[mc][ty + 1][tx + 2] - mus[mc][ty + 1][tx]);
+        const R gmy = R(0.5) * (mus[mc][ty + 2][tx + 1] - mus[mc][ty][tx + 1]);
+        const R gmz = R(0.5) * (mus[ms(k + 1)][ty + 1][tx + 1] - mus[ms(k - 1)][ty + 1][tx + 1]);
+        const R Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
+
+        R f[Q];
+        R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            f[i] = Prec<P>::decode(fs[i * g.npad + s], refs[i]);
+            rho += f[i];
+            jx += R(cx(i)) * f[i];
+            jy += R(cy(i)) * f[i];
+            jz += R(cz(i)) * f[i];
+        }
+        R ux, uy, uz;
+        guo_velocity(rho, jx, jy, jz, Fx, Fy, Fz, ux, uy, uz);
+        collide_f(f, rho, ux, uy, uz, Fx, Fy, Fz, m);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int dx = cx(i) > 0 ? xp : (cx(i) < 0 ? xm : x);
+            const int dy = cy(i) > 0 ? yp : (cy(i) < 0 ? ym : y);
+            const int dz = cz(i) > 0 ? zp : (cz(i) < 0 ? zm : z);
+            fd[i * g.npad + (long long)dz * plane + (long long)dy * g.nx + dx] = Prec<P>::encode(f[i], refs[i]);
+        }
+
+        R gg[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) gg[i] = Prec<P>::decode(gs[i * g.npad + s], refs[Q + i]);
+        collide_g(gg, ph, muc, ux, uy, uz, m);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int dx = cx(i) > 0 ? xp : (cx(i) < 0 ? xm : x);
+            const int dy = cy(i) > 0 ? yp : (cy(i) < 0 ? ym : y);
+            const int dz = cz(i) > 0 ? zp : (cz(i) < 0 ? zm : z);
+            gd[i * g.npad + (long long)dz * plane + (long long)dy * g.nx + dx] = Prec<P>::encode(gg[i], refs[Q + i]);
+        }
+    }
+}
+
+template <class R>
+Model<R> model_of(const ld_params& p) {
+    Model<R> m;
+    m.A = (R)p.A;
+    m.B = (R)p.B;
+    m.kappa = (R)p.kappa;
+    m.Gamma = (R)p.Gamma;
+    m.omega_f = (R)(1.0 / p.tau_f);
+    m.omega_g = (R)(1.0 / p.tau_g);
+    m.force_pre = (R)(1.0 - 0.5 / p.tau_f);
+    return m;
+}
+
+constexpr int kTY = 8;
+
+// Planes per CTA: the largest of 32, 16, 8, 4 dividing nz that still gives
+// at least ~8 CTAs per SM of work (152 SMs), else the smallest divisor.
+int choose_zc(int nx, int ny, int nz) {
+    const long long cols = (long long)(nx / kTX) * (ny / kTY);
+    int best = 0;
+    for (int zc = 32; zc >= 4; zc /= 2) {
+        if (nz % zc) continue;
+        best = zc;
+        if (cols * (nz / zc) >= 8LL * 152) break;
+    }
+    return best;
+}
+
+template <int P>
+cudaError_t step_fused_p(ld_ctx* c) {
+    using S = typename Prec<P>::store_t;
+    using R = typename Prec<P>::real_t;
+    const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
+    const int zc = choose_zc(g.nx, g.ny, g.nz);
+    const dim3 grid(g.nx / kTX, g.ny / kTY, g.nz / zc);
+    const int a = c->cur, b = 1 - c->cur;
+    k_step_fused<P, kTY><<<grid, kTX * kTY, 0, c->stream>>>(g, model_of<R>(c->prm), zc, (const S*)f_of(c, a),
+                                                            (const S*)g_of(c, a), (S*)f_of(c, b), (S*)g_of(c, b),
+                                                            c->ref);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fused_supported(int nx, int ny, int nz) {
+    return nx % kTX == 0 && ny % kTY == 0 && nz >= 4 && choose_zc(nx, ny, nz) > 0;
+}
+
+cudaError_t launch_step_fused(ld_ctx* c) {
+    switch (c->prec) {
+        case LD_FP64: return step_fused_p<LD_FP64>(c);
+        case LD_FP32: return step_fused_p<LD_FP32>(c);
+        case LD_FP16DEV: return step_fused_p<LD_FP16DEV>(c);
+        case LD_BF16DEV: return step_fused_p<LD_BF16DEV>(c);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ld

@@ -1,0 +1,478 @@
+// Generic kernels: any lattice size >= 4 in every dimension, one thread per
+// site. The step runs as three launches -- phi (zeroth moment of g),
+// mu (7-point stencil), and collide+propagate -- and the same file holds the
+// initialiser, the macroscopic output, the FP64 conservation sums, the
+// codec I/O and propagation alone.
+#include "ld_common.cuh"
+#include "ld_internal.h"
+
+namespace ld {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline Geom to_dev(const GeomH& h) { return Geom{h.nx, h.ny, h.nz, h.n, h.npad}; }
+
+inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+__device__ __forceinline__ void site_coords(const Geom& g, long long s, int& x, int& y, int& z) {
+    x = (int)(s % g.nx);
+    long long t = s / g.nx;
+    y = (int)(t % g.ny);
+    z = (int)(t / g.ny);
+}
+
+__device__ __forceinline__ long long site_of(const Geom& g, int x, int y, int z) {
+    return (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+}
+
+// Coordinate after a displacement of -1, 0 or +1 (periodic).
+__device__ __forceinline__ int step_coord(int a, int d, int n) {
+    return d > 0 ? wrap_inc(a, n) : (d < 0 ? wrap_dec(a, n) : a);
+}
+
+template <class R>
+Model<R> model_of(const ld_params& p) {
+    Model<R> m;
+    m.A = (R)p.A;
+    m.B = (R)p.B;
+    m.kappa = (R)p.kappa;
+    m.Gamma = (R)p.Gamma;
+    m.omega_f = (R)(1.0 / p.tau_f);
+    m.omega_g = (R)(1.0 / p.tau_g);
+    m.force_pre = (R)(1.0 - 0.5 / p.tau_f);
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// Step, stage 1: phi = sum_i g_i (pre-collision state is stored locally).
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_phi(Geom g, const typename Prec<P>::store_t* __restrict__ gs,
+                                                  const float* __restrict__ ref,
+                                                  typename Prec<P>::real_t* __restrict__ phi) {
+    using R = typename Prec<P>::real_t;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    R acc = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) acc += Prec<P>::decode(gs[i * g.npad + s], ref[Q + i]);
+    phi[s] = acc;
+}
+
+// Step, stage 2: mu = A phi + B phi^3 - kappa lap(phi).
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_mu(Geom g, Model<R> m, const R* __restrict__ phi,
+                                                 R* __restrict__ mu) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    int x, y, z;
+    site_coords(g, s, x, y, z);
+    const R p = phi[s];
+    const R lap = phi[site_of(g, wrap_inc(x, g.nx), y, z)] + phi[site_of(g, wrap_dec(x, g.nx), y, z)]
+                + phi[site_of(g, x, wrap_inc(y, g.ny), z)] + phi[site_of(g, x, wrap_dec(y, g.ny), z)]
+                + phi[site_of(g, x, y, wrap_inc(z, g.nz))] + phi[site_of(g, x, y, wrap_dec(z, g.nz))]
+                - R(6) * p;
+    mu[s] = m.A * p + m.B * p * p * p - m.kappa * lap;
+}
+
+// Step, stage 3: force, velocity, collisions of f and g, and propagation
+// (push: the post-collision value of direction i goes to x + c_i).
+template <int P>
+__global__ void __launch_bounds__(kThreads)
+    k_collide(Geom g, Model<typename Prec<P>::real_t> m, const typename Prec<P>::store_t* __restrict__ fs,
+              const typename Prec<P>::store_t* __restrict__ gs, typename Prec<P>::store_t* __restrict__ fd,
+              typename Prec<P>::store_t* __restrict__ gd, const typename Prec<P>::real_t* __restrict__ phi,
+              const typename Prec<P>::real_t* __restrict__ mu, const float* __restrict__ ref) {
+    using R = typename Prec<P>::real_t;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    int x, y, z;
+    site_coords(g, s, x, y, z);
+    const int xp = wrap_inc(x, g.nx), xm = wrap_dec(x, g.nx);
+    const int yp = wrap_inc(y, g.ny), ym = wrap_dec(y, g.ny);
+    const int zp = wrap_inc(z, g.nz), zm = wrap_dec(z, g.nz);
+
+    const R ph = phi[s];
+    const R gmx = R(0.5) * (mu[site_of(g, xp, y, z)] - mu[site_of(g, xm, y, z)]);
+    const R gmy = R(0.5) * (mu[site_of(g, x, yp, z)] - mu[site_of(g, x, ym, z)]);
+    const R gmz = R(0.5) * (mu[site_of(g, x, y, zp)] - mu[site_of(g, x, y, zm)]);
+    const R Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
+
+    R f[Q];
+    R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        f[i] = Prec<P>::decode(fs[i * g.npad + s], ref[i]);
+        rho += f[i];
+        jx += R(cx(i)) * f[i];
+        jy += R(cy(i)) * f[i];
+        jz += R(cz(i)) * f[i];
+    }
+    R ux, uy, uz;
+    guo_velocity(rho, jx, jy, jz, Fx, Fy, Fz, ux, uy, uz);
+    collide_f(f, rho, ux, uy, uz, Fx, Fy, Fz, m);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const long long d = site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny),
+                                    step_coord(z, cz(i), g.nz));
+        fd[i * g.npad + d] = Prec<P>::encode(f[i], ref[i]);
+    }
+
+    R gg[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) gg[i] = Prec<P>::decode(gs[i * g.npad + s], ref[Q + i]);
+    collide_g(gg, ph, mu[s], ux, uy, uz, m);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const long long d = site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny),
+                                    step_coord(z, cz(i), g.nz));
+        gd[i * g.npad + d] = Prec<P>::encode(gg[i], ref[Q + i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initial state: f = feq(rho, u), g = geq(phi, u, mu(phi)), in double, then
+// encoded to the storage precision.
+template <int P>
+__global__ void __launch_bounds__(kThreads)
+    k_init(Geom g, Model<double> m, double rho0, const double* __restrict__ phi,
+           const double* __restrict__ rho_in, const double* __restrict__ u_in, const float* __restrict__ ref,
+           typename Prec<P>::store_t* __restrict__ fd, typename Prec<P>::store_t* __restrict__ gd) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    int x, y, z;
+    site_coords(g, s, x, y, z);
+    const double p = phi[s];
+    const double lap = phi[site_of(g, wrap_inc(x, g.nx), y, z)] + phi[site_of(g, wrap_dec(x, g.nx), y, z)]
+                     + phi[site_of(g, x, wrap_inc(y, g.ny), z)] + phi[site_of(g, x, wrap_dec(y, g.ny), z)]
+                     + phi[site_of(g, x, y, wrap_inc(z, g.nz))] + phi[site_of(g, x, y, wrap_dec(z, g.nz))]
+                     - 6.0 * p;
+    const double mu = m.A * p + m.B * p * p * p - m.kappa * lap;
+    const double rho = rho_in ? rho_in[s] : rho0;
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    if (u_in) {
+        ux = u_in[s];
+        uy = u_in[g.n + s];
+        uz = u_in[2 * g.n + s];
+    }
+    const double uu = ux * ux + uy * uy + uz * uz;
+    const double dev = m.Gamma * mu - p / 3.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+        const double feq = wgt<double>(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        const double geq = wgt<double>(i) * (p + 3.0 * p * cu + 4.5 * dev * (c2(i) - 1) + 4.5 * p * cu * cu
+                                             - 1.5 * p * uu);
+        fd[i * g.npad + s] = Prec<P>::encode_d(feq, ref[i]);
+        gd[i * g.npad + s] = Prec<P>::encode_d(geq, ref[Q + i]);
+    }
+}
+
+// Deviation references from the total of phi (in totals[0]): f_i: w_i rho0;
+// g_i: geq_i(phibar, 0, A phibar + B phibar^3).
+__global__ void k_refs(const double* __restrict__ totals, long long n, Model<double> m, double rho0,
+                       float* __restrict__ ref) {
+    const int i = threadIdx.x;
+    if (i >= Q) return;
+    const double pb = totals[0] / (double)n;
+    const double mub = m.A * pb + m.B * pb * pb * pb;
+    ref[i] = (float)(wgt<double>(i) * rho0);
+    ref[Q + i] = (float)(wgt<double>(i) * (pb + 4.5 * (m.Gamma * mub - pb / 3.0) * (c2(i) - 1)));
+}
+
+__global__ void k_default_refs(double rho0, float* __restrict__ ref) {
+    const int i = threadIdx.x;
+    if (i >= Q) return;
+    ref[i] = (float)(wgt<double>(i) * rho0);
+    ref[Q + i] = 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic FP64 reductions: fixed grid, fixed per-thread order, fixed
+// shuffle tree; then one ordered pass over the block partials.
+template <int K>
+__device__ __forceinline__ void block_sum_store(double (&v)[K], double* __restrict__ out_block) {
+    __shared__ double red[kRedThreads / 32][K];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[warp][k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double a = lane < kRedThreads / 32 ? red[lane][k] : 0.0;
+            for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+            if (lane == 0) out_block[k] = a;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_sum_field(long long n, const double* __restrict__ x,
+                                                           double* __restrict__ partials) {
+    double v[1] = {0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += stride) v[0] += x[s];
+    block_sum_store<1>(v, partials + (long long)blockIdx.x * kRedFields);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kRedThreads)
+    k_totals(Geom g, const typename Prec<P>::store_t* __restrict__ fs,
+             const typename Prec<P>::store_t* __restrict__ gs, const float* __restrict__ ref,
+             double* __restrict__ partials) {
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.n; s += stride) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const double fi = Prec<P>::decode_d(fs[i * g.npad + s], ref[i]);
+            v[0] += fi;
+            v[2] += cx(i) * fi;
+            v[3] += cy(i) * fi;
+            v[4] += cz(i) * fi;
+            v[1] += Prec<P>::decode_d(gs[i * g.npad + s], ref[Q + i]);
+        }
+    }
+    block_sum_store<5>(v, partials + (long long)blockIdx.x * kRedFields);
+}
+
+// Final ordered pass: out[k] = sum over blocks of partials[b][k].
+__global__ void __launch_bounds__(kRedBlocks) k_finalize(const double* __restrict__ partials, int nfields,
+                                                         double* __restrict__ out) {
+    __shared__ double red[kRedBlocks / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < nfields; ++k) {
+        double a = partials[(long long)threadIdx.x * kRedFields + k];
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+        if (lane == 0) red[warp] = a;
+        __syncthreads();
+        if (warp == 0) {
+            double b = red[lane];
+            for (int off = 16; off > 0; off >>= 1) b += __shfl_down_sync(0xffffffffu, b, off);
+            if (lane == 0) out[k] = b;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Macroscopic output (double): rho, u = (j + F/2)/rho, phi, grad phi.
+template <int P>
+__global__ void __launch_bounds__(kThreads)
+    k_macros(Geom g, const typename Prec<P>::store_t* __restrict__ fs,
+             const typename Prec<P>::store_t* __restrict__ gs, const typename Prec<P>::real_t* __restrict__ phis,
+             const typename Prec<P>::real_t* __restrict__ mu, const float* __restrict__ ref,
+             double* __restrict__ rho_out, double* __restrict__ u_out, double* __restrict__ phi_out,
+             double* __restrict__ gphi_out) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    int x, y, z;
+    site_coords(g, s, x, y, z);
+    const int xp = wrap_inc(x, g.nx), xm = wrap_dec(x, g.nx);
+    const int yp = wrap_inc(y, g.ny), ym = wrap_dec(y, g.ny);
+    const int zp = wrap_inc(z, g.nz), zm = wrap_dec(z, g.nz);
+    double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, ph = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const double fi = Prec<P>::decode_d(fs[i * g.npad + s], ref[i]);
+        rho += fi;
+        jx += cx(i) * fi;
+        jy += cy(i) * fi;
+        jz += cz(i) * fi;
+        ph += Prec<P>::decode_d(gs[i * g.npad + s], ref[Q + i]);
+    }
+    if (rho_out) rho_out[s] = rho;
+    if (phi_out) phi_out[s] = ph;
+    if (u_out) {
+        const double Fx = -ph * 0.5 * ((double)mu[site_of(g, xp, y, z)] - (double)mu[site_of(g, xm, y, z)]);
+        const double Fy = -ph * 0.5 * ((double)mu[site_of(g, x, yp, z)] - (double)mu[site_of(g, x, ym, z)]);
+        const double Fz = -ph * 0.5 * ((double)mu[site_of(g, x, y, zp)] - (double)mu[site_of(g, x, y, zm)]);
+        u_out[s] = (jx + 0.5 * Fx) / rho;
+        u_out[g.n + s] = (jy + 0.5 * Fy) / rho;
+        u_out[2 * g.n + s] = (jz + 0.5 * Fz) / rho;
+    }
+    if (gphi_out) {
+        gphi_out[s] = 0.5 * ((double)phis[site_of(g, xp, y, z)] - (double)phis[site_of(g, xm, y, z)]);
+        gphi_out[g.n + s] = 0.5 * ((double)phis[site_of(g, x, yp, z)] - (double)phis[site_of(g, x, ym, z)]);
+        gphi_out[2 * g.n + s] = 0.5 * ((double)phis[site_of(g, x, y, zp)] - (double)phis[site_of(g, x, y, zm)]);
+    }
+}
+
+// Distributions out (decoded, stride n) and in (encoded).
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_decode(Geom g, const typename Prec<P>::store_t* __restrict__ src,
+                                                     const float* __restrict__ ref, double* __restrict__ out) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) out[i * g.n + s] = Prec<P>::decode_d(src[i * g.npad + s], ref[i]);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_encode(Geom g, const double* __restrict__ in,
+                                                     const float* __restrict__ ref,
+                                                     typename Prec<P>::store_t* __restrict__ dst) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dst[i * g.npad + s] = Prec<P>::encode_d(in[i * g.n + s], ref[i]);
+}
+
+// Propagation alone on raw storage words (T has the storage width).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_propagate(Geom g, int reverse, const T* __restrict__ src,
+                                                        T* __restrict__ dst) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    int x, y, z;
+    site_coords(g, s, x, y, z);
+#pragma unroll
+    for (int i = 0; i < 2 * Q; ++i) {  // f components then g components
+        const int q = i % Q;
+        const long long o = site_of(g, step_coord(x, cx(q), g.nx), step_coord(y, cy(q), g.ny),
+                                    step_coord(z, cz(q), g.nz));
+        if (reverse)
+            dst[i * g.npad + s] = src[i * g.npad + o];
+        else
+            dst[i * g.npad + o] = src[i * g.npad + s];
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <int P>
+cudaError_t init_p(ld_ctx* c, const double* phi, const double* rho, const double* u) {
+    using S = typename Prec<P>::store_t;
+    const Geom g = to_dev(c->geom);
+    const Model<double> m = model_of<double>(c->prm);
+    if (Prec<P>::kDev) {
+        k_sum_field<<<kRedBlocks, kRedThreads, 0, c->stream>>>(g.n, phi, c->partials);
+        k_finalize<<<1, kRedBlocks, 0, c->stream>>>(c->partials, 1, c->totals);
+        k_refs<<<1, 32, 0, c->stream>>>(c->totals, g.n, m, c->prm.rho0, c->ref);
+    } else {
+        k_default_refs<<<1, 32, 0, c->stream>>>(c->prm.rho0, c->ref);
+    }
+    k_init<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, m, c->prm.rho0, phi, rho, u, c->ref,
+                                                           (S*)f_of(c, c->cur), (S*)g_of(c, c->cur));
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t phi_mu_p(ld_ctx* c, int buf) {
+    using S = typename Prec<P>::store_t;
+    using R = typename Prec<P>::real_t;
+    const Geom g = to_dev(c->geom);
+    k_phi<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, (const S*)g_of(c, buf), c->ref, (R*)c->phi);
+    k_mu<R><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, model_of<R>(c->prm), (const R*)c->phi, (R*)c->mu);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t collide_p(ld_ctx* c) {
+    using S = typename Prec<P>::store_t;
+    using R = typename Prec<P>::real_t;
+    const Geom g = to_dev(c->geom);
+    const int a = c->cur, b = 1 - c->cur;
+    k_collide<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(
+        g, model_of<R>(c->prm), (const S*)f_of(c, a), (const S*)g_of(c, a), (S*)f_of(c, b), (S*)g_of(c, b),
+        (const R*)c->phi, (const R*)c->mu, c->ref);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t macros_p(ld_ctx* c, double* rho, double* u, double* phi, double* gphi) {
+    using S = typename Prec<P>::store_t;
+    using R = typename Prec<P>::real_t;
+    const Geom g = to_dev(c->geom);
+    cudaError_t e = phi_mu_p<P>(c, c->cur);
+    if (e != cudaSuccess) return e;
+    k_macros<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, (const S*)f_of(c, c->cur), (const S*)g_of(c, c->cur),
+                                                             (const R*)c->phi, (const R*)c->mu, c->ref, rho, u,
+                                                             phi, gphi);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t totals_p(ld_ctx* c, double* out) {
+    using S = typename Prec<P>::store_t;
+    const Geom g = to_dev(c->geom);
+    k_totals<P><<<kRedBlocks, kRedThreads, 0, c->stream>>>(g, (const S*)f_of(c, c->cur), (const S*)g_of(c, c->cur),
+                                                           c->ref, c->partials);
+    k_finalize<<<1, kRedBlocks, 0, c->stream>>>(c->partials, 5, out);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t decode_p(ld_ctx* c, double* f, double* gout) {
+    using S = typename Prec<P>::store_t;
+    const Geom g = to_dev(c->geom);
+    if (f) k_decode<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, (const S*)f_of(c, c->cur), c->ref, f);
+    if (gout)
+        k_decode<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, (const S*)g_of(c, c->cur), c->ref + Q, gout);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t encode_p(ld_ctx* c, const double* f, const double* gin) {
+    using S = typename Prec<P>::store_t;
+    const Geom g = to_dev(c->geom);
+    if (f) k_encode<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, f, c->ref, (S*)f_of(c, c->cur));
+    if (gin) k_encode<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, gin, c->ref + Q, (S*)g_of(c, c->cur));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+#define LD_DISPATCH(fn, ...)                                        \
+    switch (c->prec) {                                              \
+        case LD_FP64: return fn<LD_FP64>(__VA_ARGS__);              \
+        case LD_FP32: return fn<LD_FP32>(__VA_ARGS__);              \
+        case LD_FP16DEV: return fn<LD_FP16DEV>(__VA_ARGS__);        \
+        case LD_BF16DEV: return fn<LD_BF16DEV>(__VA_ARGS__);        \
+        default: return cudaErrorInvalidValue;                      \
+    }
+
+cudaError_t launch_init(ld_ctx* c, const double* phi, const double* rho, const double* u) {
+    LD_DISPATCH(init_p, c, phi, rho, u);
+}
+cudaError_t launch_phi_mu(ld_ctx* c, int buf) { LD_DISPATCH(phi_mu_p, c, buf); }
+cudaError_t launch_collide_generic(ld_ctx* c) { LD_DISPATCH(collide_p, c); }
+cudaError_t launch_macros(ld_ctx* c, double* rho, double* u, double* phi, double* gphi) {
+    LD_DISPATCH(macros_p, c, rho, u, phi, gphi);
+}
+cudaError_t launch_totals(ld_ctx* c, double* totals) { LD_DISPATCH(totals_p, c, totals); }
+cudaError_t launch_decode(ld_ctx* c, double* f, double* g) { LD_DISPATCH(decode_p, c, f, g); }
+cudaError_t launch_encode(ld_ctx* c, const double* f, const double* g) { LD_DISPATCH(encode_p, c, f, g); }
+
+cudaError_t launch_default_refs(ld_ctx* c) {
+    k_default_refs<<<1, 32, 0, c->stream>>>(c->prm.rho0, c->ref);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propagate(ld_ctx* c, int reverse) {
+    const Geom g = to_dev(c->geom);
+    const void* src = c->dist[c->cur];
+    void* dst = c->dist[1 - c->cur];
+    const unsigned nb = blocks_for(g.n);
+    switch (c->store_bytes) {
+        case 8:
+            k_propagate<unsigned long long><<<nb, kThreads, 0, c->stream>>>(g, reverse, (const unsigned long long*)src,
+                                                                            (unsigned long long*)dst);
+            break;
+        case 4:
+            k_propagate<unsigned int><<<nb, kThreads, 0, c->stream>>>(g, reverse, (const unsigned int*)src,
+                                                                      (unsigned int*)dst);
+            break;
+        case 2:
+            k_propagate<unsigned short><<<nb, kThreads, 0, c->stream>>>(g, reverse, (const unsigned short*)src,
+                                                                        (unsigned short*)dst);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ld

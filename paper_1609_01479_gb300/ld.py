@@ -1,0 +1,280 @@
+"""Python binding of libld (include/ld.h): argument marshalling only.
+
+Every function named ``ld_*`` here calls the C function of the same name
+through ctypes with raw device pointers taken from torch tensors; all
+arithmetic of the lattice-Boltzmann step runs in the library's CUDA kernels.
+PyTorch supplies device memory (the workspace, checkpoints, inputs and
+outputs) and the CUDA stream. There is no CPU fallback: if libld.so cannot be
+built or loaded, every call raises.
+
+``LdSim`` bundles a context with its torch-owned workspace for convenience.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import build as _build
+
+LD_FP64, LD_FP32, LD_FP16DEV, LD_BF16DEV = 0, 1, 2, 3
+LD_KERNEL_AUTO, LD_KERNEL_GENERIC, LD_KERNEL_FUSED = 0, 1, 2
+LD_OK, LD_EINVAL, LD_ECUDA, LD_ENONFINITE, LD_ESTATE = 0, -1, -2, -3, -4
+
+PRECISIONS = {"fp64": LD_FP64, "fp32": LD_FP32, "fp16dev": LD_FP16DEV, "bf16dev": LD_BF16DEV}
+KERNELS = {"auto": LD_KERNEL_AUTO, "generic": LD_KERNEL_GENERIC, "fused": LD_KERNEL_FUSED}
+STORE_BYTES = {LD_FP64: 8, LD_FP32: 4, LD_FP16DEV: 2, LD_BF16DEV: 2}
+Q = 19
+
+
+class LdParams(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_double), ("B", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("Gamma", ctypes.c_double), ("tau_f", ctypes.c_double), ("tau_g", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("precision", ctypes.c_int), ("kernel", ctypes.c_int)]
+
+
+class LdError(RuntimeError):
+    def __init__(self, code: int, where: str, message: str):
+        super().__init__(f"{where} failed ({code}): {message}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+# Signatures of every exported entry point (include/ld.h).
+_VP = ctypes.c_void_p
+_SIGNATURES = {
+    "ld_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(LdParams)]),
+    "ld_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(LdParams), _VP,
+                                 ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+    "ld_destroy": (ctypes.c_int, [_VP]),
+    "ld_set_stream": (ctypes.c_int, [_VP, _VP]),
+    "ld_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(LdParams)]),
+    "ld_init": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "ld_step": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "ld_moments": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "ld_check": (ctypes.c_int, [_VP]),
+    "ld_get_distributions": (ctypes.c_int, [_VP, _VP, _VP]),
+    "ld_set_distributions": (ctypes.c_int, [_VP, _VP, _VP]),
+    "ld_propagate": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "ld_state_bytes": (ctypes.c_size_t, [_VP]),
+    "ld_save_state": (ctypes.c_int, [_VP, _VP]),
+    "ld_load_state": (ctypes.c_int, [_VP, _VP]),
+    "ld_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "ld_last_error": (ctypes.c_char_p, [_VP]),
+}
+
+
+def lib():
+    """Load libld.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            handle = ctypes.CDLL(path)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(handle, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = handle
+        return _lib
+
+
+def _ptr(t):
+    """Device pointer of a tensor (or None)."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _call(name, ctx, *args):
+    rc = getattr(lib(), name)(ctx, *args)
+    if rc != LD_OK:
+        msg = lib().ld_last_error(ctx).decode(errors="replace")
+        raise LdError(rc, name, msg)
+    return rc
+
+
+def make_params(A=-0.0625, B=0.0625, kappa=0.04, Gamma=0.5, tau_f=1.0, tau_g=1.0, rho0=1.0,
+                precision="fp32", kernel="auto") -> LdParams:
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    kern = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    return LdParams(A, B, kappa, Gamma, tau_f, tau_g, rho0, prec, kern)
+
+
+# ---------------------------------------------------------------------------
+# Same-named wrappers of the C entry points.
+
+def ld_workspace_bytes(nx, ny, nz, params: LdParams) -> int:
+    return int(lib().ld_workspace_bytes(nx, ny, nz, ctypes.byref(params)))
+
+
+def ld_create(nx, ny, nz, params: LdParams, workspace: torch.Tensor, stream=None):
+    out = ctypes.c_void_p()
+    ws = _ptr(workspace)
+    nbytes = workspace.numel() * workspace.element_size()
+    s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream(workspace.device).cuda_stream)
+    rc = lib().ld_create(nx, ny, nz, ctypes.byref(params), ws, nbytes, s, ctypes.byref(out))
+    if rc != LD_OK:
+        raise LdError(rc, "ld_create", lib().ld_last_error(None).decode(errors="replace"))
+    return out
+
+
+def ld_destroy(ctx):
+    return lib().ld_destroy(ctx)
+
+
+def ld_set_stream(ctx, stream: int):
+    return _call("ld_set_stream", ctx, ctypes.c_void_p(stream))
+
+
+def ld_set_params(ctx, params: LdParams):
+    return _call("ld_set_params", ctx, ctypes.byref(params))
+
+
+def ld_init(ctx, phi, rho=None, u=None):
+    return _call("ld_init", ctx, _ptr(phi), _ptr(rho), _ptr(u))
+
+
+def ld_step(ctx, nsteps: int):
+    return _call("ld_step", ctx, int(nsteps))
+
+
+def ld_moments(ctx, rho=None, u=None, phi=None, grad_phi=None, totals=None):
+    return _call("ld_moments", ctx, _ptr(rho), _ptr(u), _ptr(phi), _ptr(grad_phi), _ptr(totals))
+
+
+def ld_check(ctx):
+    return _call("ld_check", ctx)
+
+
+def ld_get_distributions(ctx, f=None, g=None):
+    return _call("ld_get_distributions", ctx, _ptr(f), _ptr(g))
+
+
+def ld_set_distributions(ctx, f, g):
+    return _call("ld_set_distributions", ctx, _ptr(f), _ptr(g))
+
+
+def ld_propagate(ctx, reverse: bool = False):
+    return _call("ld_propagate", ctx, int(bool(reverse)))
+
+
+def ld_state_bytes(ctx) -> int:
+    return int(lib().ld_state_bytes(ctx))
+
+
+def ld_save_state(ctx, buf):
+    return _call("ld_save_state", ctx, _ptr(buf))
+
+
+def ld_load_state(ctx, buf):
+    return _call("ld_load_state", ctx, _ptr(buf))
+
+
+def ld_strerror(code: int) -> str:
+    return lib().ld_strerror(code).decode()
+
+
+def ld_last_error(ctx=None) -> str:
+    return lib().ld_last_error(ctx).decode(errors="replace")
+
+
+# ---------------------------------------------------------------------------
+class LdSim:
+    """A lattice with its torch-owned workspace and a library context.
+
+    Fields are torch float64 CUDA tensors shaped (nz, ny, nx) (vectors
+    (3, nz, ny, nx), distributions (19, nz, ny, nx)), site order x fastest.
+    """
+
+    def __init__(self, nx, ny, nz, precision="fp32", kernel="auto", device="cuda", stream=None, **model):
+        self.shape = (nz, ny, nx)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.n = nx * ny * nz
+        self.device = torch.device(device)
+        self.params = make_params(precision=precision, kernel=kernel, **model)
+        nbytes = ld_workspace_bytes(nx, ny, nz, self.params)
+        if nbytes == 0:
+            raise LdError(LD_EINVAL, "ld_workspace_bytes", "invalid lattice size or parameters")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.ctx = ld_create(nx, ny, nz, self.params, self.workspace, stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ld_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _field(self, *lead):
+        return torch.empty(*lead, *self.shape, dtype=torch.float64, device=self.device)
+
+    def set_params(self, **model):
+        p = self.params
+        kw = {f[0]: getattr(p, f[0]) for f in LdParams._fields_}
+        kw.update(model)
+        self.params = LdParams(*[kw[f[0]] for f in LdParams._fields_])
+        ld_set_params(self.ctx, self.params)
+
+    def init(self, phi, rho=None, u=None):
+        phi = torch.as_tensor(phi, dtype=torch.float64, device=self.device).contiguous()
+        rho = None if rho is None else torch.as_tensor(rho, dtype=torch.float64, device=self.device).contiguous()
+        u = None if u is None else torch.as_tensor(u, dtype=torch.float64, device=self.device).contiguous()
+        self._inputs = (phi, rho, u)  # kept alive until the stream has consumed them
+        ld_init(self.ctx, phi, rho, u)
+
+    def step(self, nsteps=1):
+        ld_step(self.ctx, nsteps)
+
+    def moments(self, grad_phi=False):
+        out = dict(rho=self._field(), u=self._field(3), phi=self._field(),
+                   totals=torch.empty(5, dtype=torch.float64, device=self.device))
+        if grad_phi:
+            out["grad_phi"] = self._field(3)
+        ld_moments(self.ctx, out["rho"], out["u"], out["phi"], out.get("grad_phi"), out["totals"])
+        return out
+
+    def totals(self):
+        t = torch.empty(5, dtype=torch.float64, device=self.device)
+        ld_moments(self.ctx, totals=t)
+        return t
+
+    def check(self):
+        ld_check(self.ctx)
+
+    def distributions(self):
+        f, g = self._field(Q), self._field(Q)
+        ld_get_distributions(self.ctx, f, g)
+        return f, g
+
+    def set_distributions(self, f, g):
+        f = torch.as_tensor(f, dtype=torch.float64, device=self.device).contiguous()
+        g = torch.as_tensor(g, dtype=torch.float64, device=self.device).contiguous()
+        self._inputs = (f, g)
+        ld_set_distributions(self.ctx, f, g)
+
+    def propagate(self, reverse=False):
+        ld_propagate(self.ctx, reverse)
+
+    def save_state(self, buf=None):
+        if buf is None:
+            buf = torch.empty(ld_state_bytes(self.ctx), dtype=torch.uint8, device=self.device)
+        ld_save_state(self.ctx, buf)
+        return buf
+
+    def load_state(self, buf):
+        ld_load_state(self.ctx, buf)
