@@ -77,7 +77,7 @@ def measured_hbm_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for rel in ("paper_1609_01479_gb300/csrc/ld_fused.cu", "paper_1609_01479_gb300/csrc/ld_common.cuh"):
+    for rel in ("paper_1609_01479_gb300/csrc/ld_fused.cuh", "paper_1609_01479_gb300/csrc/ld_common.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -390,7 +390,7 @@ def main():
         "config": cfg,
         "roofline": {"bound": "hbm", "achieved": P["algorithmic_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": P["roofline_frac"], "traffic": traffic,
-                     "kernel": "k_step_fused" if True else None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                     "kernel": "k_step_fused", "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
                      "per_site_bytes": P["bytes_per_site"], "kernel_ms": P["kernel_ms"]},
         "clocks": P["clocks"],

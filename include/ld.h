@@ -52,9 +52,16 @@ extern "C" {
  * phibar the mean of the initial phi; stores round to nearest even. */
 enum { LD_FP64 = 0, LD_FP32 = 1, LD_FP16DEV = 2, LD_BF16DEV = 3 };
 
-/* Step kernel selection: LD_KERNEL_AUTO picks the fused kernel when the lattice
- * admits it (nx % 32 == 0, ny % 8 == 0, nz % 4 == 0), else the generic one. */
-enum { LD_KERNEL_AUTO = 0, LD_KERNEL_GENERIC = 1, LD_KERNEL_FUSED = 2 };
+/* Step kernel selection.
+ * LD_KERNEL_GENERIC: three launches per step (phi, mu, collide+propagate); any lattice.
+ * LD_KERNEL_FUSED: one launch per step that reads and writes each distribution
+ *   once from HBM; phi and mu rings in shared memory, distributions through
+ *   registers (nx % 32 == 0, ny % 8 == 0, nz % 4 == 0).
+ * LD_KERNEL_FUSED_TMA: the fused step with each plane's distributions staged
+ *   in shared memory by TMA bulk copies; FP32 and the 16-bit forms only
+ *   (nx % 32 == 0, ny % 8 == 0, nz % 4 == 0).
+ * LD_KERNEL_AUTO: FUSED when the lattice admits it, else GENERIC. */
+enum { LD_KERNEL_AUTO = 0, LD_KERNEL_GENERIC = 1, LD_KERNEL_FUSED = 2, LD_KERNEL_FUSED_TMA = 3 };
 
 enum {
     LD_OK = 0,
@@ -69,7 +76,7 @@ typedef struct {
     double tau_f, tau_g;       /* relaxation times, each > 1/2 */
     double rho0;               /* reference density (default rho, f deviation reference) */
     int precision;             /* LD_FP64 .. LD_BF16DEV */
-    int kernel;                /* LD_KERNEL_AUTO / GENERIC / FUSED */
+    int kernel;                /* LD_KERNEL_AUTO / GENERIC / FUSED / FUSED_TMA */
 } ld_params;
 
 typedef struct ld_ctx ld_ctx;
@@ -113,7 +120,9 @@ int ld_step(ld_ctx* ctx, int nsteps);
 int ld_moments(ld_ctx* ctx, double* rho, double* u, double* phi, double* grad_phi, double* totals);
 
 /* Synchronise the stream and return LD_ENONFINITE if the state holds a NaN
- * or Inf (tested through the FP64 totals), else LD_OK. Blocks the host. */
+ * or Inf (tested through the FP64 totals), LD_ECUDA if a kernel recorded that
+ * it gave up waiting for its shared-memory copies, else LD_OK. Blocks the
+ * host. */
 int ld_check(ld_ctx* ctx);
 
 /* Copy the current pre-collision distributions out as double[19][N] each

@@ -59,7 +59,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
-        cmd = [exe, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+        # the FP64 unit rounds every operation separately (no FMA contraction)
+        per_file = ["-fmad=false"] if src.endswith("_f64.cu") else []
+        cmd = [exe, *ARCH, *NVCC_FLAGS, *per_file, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")

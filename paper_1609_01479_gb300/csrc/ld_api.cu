@@ -33,7 +33,7 @@ size_t real_bytes_of(int prec) { return prec == LD_FP64 ? 8 : 4; }
 long long npad_of(long long n) { return (n + 63) / 64 * 64; }
 
 struct Layout {
-    size_t dist, phi, mu, partials, totals, ref, total;
+    size_t dist, phi, mu, partials, totals, ref, status, total;
 };
 
 Layout layout_of(int nx, int ny, int nz, int prec) {
@@ -53,6 +53,8 @@ Layout layout_of(int nx, int ny, int nz, int prec) {
     off += align_up(sizeof(double) * 8);
     L.ref = off;
     off += align_up(sizeof(float) * 2 * kQ);
+    L.status = off;
+    off += align_up(sizeof(int));
     L.total = off;
     return L;
 }
@@ -78,7 +80,7 @@ bool params_ok(const ld_params* p, const char** why) {
     if (!isfinite(p->A) || !isfinite(p->B) || !isfinite(p->kappa) || !isfinite(p->Gamma))
         return *why = "A, B, kappa, Gamma must be finite", false;
     if (p->precision < LD_FP64 || p->precision > LD_BF16DEV) return *why = "unknown precision", false;
-    if (p->kernel < LD_KERNEL_AUTO || p->kernel > LD_KERNEL_FUSED) return *why = "unknown kernel", false;
+    if (p->kernel < LD_KERNEL_AUTO || p->kernel > LD_KERNEL_FUSED_TMA) return *why = "unknown kernel", false;
     return true;
 }
 
@@ -133,9 +135,10 @@ int ld_create(int nx, int ny, int nz, const ld_params* p, void* dev_workspace, s
     if ((uintptr_t)dev_workspace % kAlign) return fail(nullptr, LD_EINVAL, "workspace must be 256-byte aligned");
     if (bytes < L.total)
         return fail(nullptr, LD_EINVAL, "workspace of %zu bytes is smaller than the %zu needed", bytes, L.total);
-    const bool fused_ok = ld::fused_supported(nx, ny, nz);
-    if (p->kernel == LD_KERNEL_FUSED && !fused_ok)
-        return fail(nullptr, LD_EINVAL, "fused kernel needs nx %% 32 == 0, ny %% 8 == 0, nz %% 4 == 0");
+    const int step_kernel = ld::choose_step_kernel(nx, ny, nz, p->precision, p->kernel);
+    if (step_kernel == 0)
+        return fail(nullptr, LD_EINVAL,
+                    "fused kernels need nx %% 32 == 0, ny %% 8 == 0, nz %% 4 == 0 (TMA: FP32/FP16DEV/BF16DEV only)");
 
     ld_ctx* c = (ld_ctx*)calloc(1, sizeof(ld_ctx));
     if (!c) return fail(nullptr, LD_EINVAL, "host allocation of the context failed");
@@ -159,11 +162,21 @@ int ld_create(int nx, int ny, int nz, const ld_params* p, void* dev_workspace, s
     c->partials = (double*)(c->ws + L.partials);
     c->totals = (double*)(c->ws + L.totals);
     c->ref = (float*)(c->ws + L.ref);
+    c->status = (int*)(c->ws + L.status);
     c->stream = (cudaStream_t)cuda_stream;
     c->initialized = false;
-    c->fused = p->kernel == LD_KERNEL_FUSED || (p->kernel == LD_KERNEL_AUTO && fused_ok);
+    c->step_kernel = step_kernel;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            c->num_sms = sms;
+        else
+            c->num_sms = 152;
+    }
     c->last_error[0] = '\0';
-    cudaError_t e = ld::launch_default_refs(c);
+    cudaError_t e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = ld::launch_default_refs(c);
     if (e != cudaSuccess) {
         int rc = cuda_fail(nullptr, e, "ld_create");
         free(c);
@@ -211,7 +224,7 @@ int ld_step(ld_ctx* c, int nsteps) {
     if (nsteps < 0) return fail(c, LD_EINVAL, "nsteps must be >= 0");
     for (int t = 0; t < nsteps; ++t) {
         cudaError_t e;
-        if (c->fused) {
+        if (c->step_kernel != ld::kStepGeneric) {
             e = ld::launch_step_fused(c);
         } else {
             e = ld::launch_phi_mu(c, c->cur);
@@ -239,10 +252,13 @@ int ld_check(ld_ctx* c) {
     int rc = check_ready(c);
     if (rc) return rc;
     double host[5];
+    int status = 0;
     cudaError_t e = ld::launch_totals(c, c->totals);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host, c->totals, sizeof(host), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ld_check");
+    if (status) return fail(c, LD_ECUDA, "a kernel gave up waiting for its shared-memory copies (status %d)", status);
     for (int k = 0; k < 5; ++k)
         if (!isfinite(host[k])) return fail(c, LD_ENONFINITE, "state holds a non-finite value (total %d)", k);
     return LD_OK;

@@ -93,6 +93,20 @@ struct Model {
     R force_pre;         // 1 - 1/(2 tau_f)
 };
 
+// Model constants from the C-ABI parameters.
+template <class R>
+inline Model<R> model_of(const ld_params& p) {
+    Model<R> m;
+    m.A = (R)p.A;
+    m.B = (R)p.B;
+    m.kappa = (R)p.kappa;
+    m.Gamma = (R)p.Gamma;
+    m.omega_f = (R)(1.0 / p.tau_f);
+    m.omega_g = (R)(1.0 / p.tau_g);
+    m.force_pre = (R)(1.0 - 0.5 / p.tau_f);
+    return m;
+}
+
 // Reference values of the deviation codec: ref[i] for f, ref[19 + i] for g.
 constexpr int kRefCount = 2 * Q;
 
@@ -102,14 +116,52 @@ __device__ __forceinline__ int wrap_dec(int a, int n) { return a == 0 ? n - 1 : 
 // ---------------------------------------------------------------------------
 // Per-site physics (one site, registers only).
 
-// Guo velocity from the moments and the force.
+// c_i . (ax, ay, az) over the nonzero components of c_i only, in x, y, z
+// order. Equal, bit for bit, to the full three-term sum (adding a zero
+// product changes nothing) without the multiplies by 0 and +-1 that IEEE
+// arithmetic does not let the compiler drop.
 template <class R>
-__device__ __forceinline__ void guo_velocity(R rho, R jx, R jy, R jz, R Fx, R Fy, R Fz, R& ux, R& uy,
-                                             R& uz) {
-    const R inv = R(1) / rho;
-    ux = (jx + R(0.5) * Fx) * inv;
-    uy = (jy + R(0.5) * Fy) * inv;
-    uz = (jz + R(0.5) * Fz) * inv;
+__device__ __forceinline__ R cdot(int i, R ax, R ay, R az) {
+    R s = R(0);
+    bool any = false;
+    if (cx(i) != 0) {
+        s = cx(i) > 0 ? ax : -ax;
+        any = true;
+    }
+    if (cy(i) != 0) {
+        s = any ? (cy(i) > 0 ? s + ay : s - ay) : (cy(i) > 0 ? ay : -ay);
+        any = true;
+    }
+    if (cz(i) != 0) s = any ? (cz(i) > 0 ? s + az : s - az) : (cz(i) > 0 ? az : -az);
+    return s;
+}
+
+// Accumulate v c_i into (jx, jy, jz), skipping zero components.
+template <class R>
+__device__ __forceinline__ void add_c(int i, R v, R& jx, R& jy, R& jz) {
+    if (cx(i) > 0) jx += v;
+    if (cx(i) < 0) jx -= v;
+    if (cy(i) > 0) jy += v;
+    if (cy(i) < 0) jy -= v;
+    if (cz(i) > 0) jz += v;
+    if (cz(i) < 0) jz -= v;
+}
+
+// Guo velocity from the moments and the force: u = (j + F/2) / rho. FP64
+// divides (the rounding the FP64 path is held to); FP32 multiplies by the
+// correctly rounded reciprocal.
+__device__ __forceinline__ void guo_velocity(double rho, double jx, double jy, double jz, double Fx, double Fy,
+                                             double Fz, double& ux, double& uy, double& uz) {
+    ux = (jx + 0.5 * Fx) / rho;
+    uy = (jy + 0.5 * Fy) / rho;
+    uz = (jz + 0.5 * Fz) / rho;
+}
+__device__ __forceinline__ void guo_velocity(float rho, float jx, float jy, float jz, float Fx, float Fy, float Fz,
+                                             float& ux, float& uy, float& uz) {
+    const float inv = __frcp_rn(rho);
+    ux = (jx + 0.5f * Fx) * inv;
+    uy = (jy + 0.5f * Fy) * inv;
+    uz = (jz + 0.5f * Fz) * inv;
 }
 
 // BGK + Guo collision of f in place.
@@ -120,8 +172,8 @@ __device__ __forceinline__ void collide_f(R (&f)[Q], R rho, R ux, R uy, R uz, R 
     const R uF = ux * Fx + uy * Fy + uz * Fz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const R cu = R(cx(i)) * ux + R(cy(i)) * uy + R(cz(i)) * uz;
-        const R cF = R(cx(i)) * Fx + R(cy(i)) * Fy + R(cz(i)) * Fz;
+        const R cu = cdot(i, ux, uy, uz);
+        const R cF = cdot(i, Fx, Fy, Fz);
         const R feq = wgt<R>(i) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
         const R src = m.force_pre * wgt<R>(i) * (R(3) * (cF - uF) + R(9) * cu * cF);
         f[i] = f[i] - m.omega_f * (f[i] - feq) + src;
@@ -132,10 +184,10 @@ __device__ __forceinline__ void collide_f(R (&f)[Q], R rho, R ux, R uy, R uz, R 
 template <class R>
 __device__ __forceinline__ void collide_g(R (&g)[Q], R phi, R mu, R ux, R uy, R uz, const Model<R>& m) {
     const R uu = ux * ux + uy * uy + uz * uz;
-    const R dev = m.Gamma * mu - phi * (R(1) / R(3));
+    const R dev = m.Gamma * mu - phi / R(3);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const R cu = R(cx(i)) * ux + R(cy(i)) * uy + R(cz(i)) * uz;
+        const R cu = cdot(i, ux, uy, uz);
         const R geq = wgt<R>(i) * (phi + R(3) * phi * cu + R(4.5) * dev * R(c2(i) - 1)
                                    + R(4.5) * phi * cu * cu - R(1.5) * phi * uu);
         g[i] = g[i] - m.omega_g * (g[i] - geq);

@@ -13,6 +13,9 @@
 // of plane k is read again for the collision two planes after phi(k) read
 // it; that second read and the halo reads of neighbouring tiles are served by
 // L2. Propagation writes into the other buffer of the ping-pong pair.
+// Template only: instantiated per storage precision by ld_prec_f64.cu and
+// ld_prec_lp.cu.
+#pragma once
 #include "ld_common.cuh"
 #include "ld_internal.h"
 
@@ -21,13 +24,11 @@ namespace {
 
 constexpr int kTX = 32;
 
-__device__ __forceinline__ int wrap_any(int a, int n) {
-    a %= n;
-    return a < 0 ? a + n : a;
-}
+// Periodic image of a coordinate at most one period outside [0, n).
+__device__ __forceinline__ int wrap_once(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 template <int P, int TY>
-__global__ void __launch_bounds__(kTX * TY)
+__global__ void __launch_bounds__(kTX * TY, 2)
     k_step_fused(Geom g, Model<typename Prec<P>::real_t> m, int zc,
                  const typename Prec<P>::store_t* __restrict__ fs, const typename Prec<P>::store_t* __restrict__ gs,
                  typename Prec<P>::store_t* __restrict__ fd, typename Prec<P>::store_t* __restrict__ gd,
@@ -43,20 +44,22 @@ __global__ void __launch_bounds__(kTX * TY)
     const int tid = threadIdx.x;
     const int tx = tid % kTX, ty = tid / kTX;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
-    const long long plane = (long long)g.nx * g.ny;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int plane = nx * ny;
+    const long long npad = g.npad;
     if (tid < 2 * Q) refs[tid] = ref_g[tid];
     __syncthreads();
 
     // phi of plane zp over the tile + 2-halo, into ring slot `slot`.
     auto phi_plane = [&](int zp, int slot) {
-        const long long zoff = (long long)wrap_any(zp, g.nz) * plane;
+        const int zoff = wrap_once(zp, nz) * plane;
         for (int idx = tid; idx < PW * PH; idx += NT) {
             const int hx = idx % PW, hy = idx / PW;
-            const int gx = wrap_any(x0 + hx - 2, g.nx), gy = wrap_any(y0 + hy - 2, g.ny);
-            const long long s = zoff + (long long)gy * g.nx + gx;
+            const int gx = wrap_once(x0 + hx - 2, nx), gy = wrap_once(y0 + hy - 2, ny);
+            const int s = zoff + gy * nx + gx;
             R acc = R(0);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) acc += Prec<P>::decode(gs[i * g.npad + s], refs[Q + i]);
+            for (int i = 0; i < Q; ++i) acc += Prec<P>::decode(gs[i * npad + s], refs[Q + i]);
             phis[slot][hy][hx] = acc;
         }
     };
@@ -86,8 +89,8 @@ __global__ void __launch_bounds__(kTX * TY)
     mu_plane(ms(z0), ps(z0 - 1), ps(z0), ps(z0 + 1));
 
     const int x = x0 + tx, y = y0 + ty;
-    const int xp = wrap_inc(x, g.nx), xm = wrap_dec(x, g.nx);
-    const int yp = wrap_inc(y, g.ny), ym = wrap_dec(y, g.ny);
+    const int oxp = x + 1 == nx ? 1 - nx : 1, oxm = x == 0 ? nx - 1 : -1;
+    const int oyp = y + 1 == ny ? (1 - ny) * nx : nx, oym = y == 0 ? (ny - 1) * nx : -nx;
 
     for (int k = z0; k < z0 + zc; ++k) {
         __syncthreads();  // previous collision done with phi(k-1) and mu(k-2) slots
@@ -96,9 +99,9 @@ __global__ void __launch_bounds__(kTX * TY)
         mu_plane(ms(k + 1), ps(k), ps(k + 1), ps(k + 2));
         __syncthreads();
 
-        const int z = k >= g.nz ? k - g.nz : k;
-        const int zp = wrap_inc(z, g.nz), zm = wrap_dec(z, g.nz);
-        const long long s = (long long)z * plane + (long long)y * g.nx + x;
+        const int z = k;  // zc divides nz: k < nz
+        const int ozp = z + 1 == nz ? (1 - nz) * plane : plane, ozm = z == 0 ? (nz - 1) * plane : -plane;
+        const int s = z * plane + y * nx + x;
         const R ph = phis[ps(k)][ty + 2][tx + 2];
         const int mc = ms(k);
         const R muc = mus[mc][ty + 1][tx + 1];
@@ -111,48 +114,31 @@ __global__ void __launch_bounds__(kTX * TY)
         R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            f[i] = Prec<P>::decode(fs[i * g.npad + s], refs[i]);
+            f[i] = Prec<P>::decode(fs[i * npad + s], refs[i]);
             rho += f[i];
-            jx += R(cx(i)) * f[i];
-            jy += R(cy(i)) * f[i];
-            jz += R(cz(i)) * f[i];
+            add_c(i, f[i], jx, jy, jz);
         }
         R ux, uy, uz;
         guo_velocity(rho, jx, jy, jz, Fx, Fy, Fz, ux, uy, uz);
         collide_f(f, rho, ux, uy, uz, Fx, Fy, Fz, m);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const int dx = cx(i) > 0 ? xp : (cx(i) < 0 ? xm : x);
-            const int dy = cy(i) > 0 ? yp : (cy(i) < 0 ? ym : y);
-            const int dz = cz(i) > 0 ? zp : (cz(i) < 0 ? zm : z);
-            fd[i * g.npad + (long long)dz * plane + (long long)dy * g.nx + dx] = Prec<P>::encode(f[i], refs[i]);
+            const int d = s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
+                          (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
+            __stcs(fd + i * npad + d, Prec<P>::encode(f[i], refs[i]));
         }
 
         R gg[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) gg[i] = Prec<P>::decode(gs[i * g.npad + s], refs[Q + i]);
+        for (int i = 0; i < Q; ++i) gg[i] = Prec<P>::decode(gs[i * npad + s], refs[Q + i]);
         collide_g(gg, ph, muc, ux, uy, uz, m);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const int dx = cx(i) > 0 ? xp : (cx(i) < 0 ? xm : x);
-            const int dy = cy(i) > 0 ? yp : (cy(i) < 0 ? ym : y);
-            const int dz = cz(i) > 0 ? zp : (cz(i) < 0 ? zm : z);
-            gd[i * g.npad + (long long)dz * plane + (long long)dy * g.nx + dx] = Prec<P>::encode(gg[i], refs[Q + i]);
+            const int d = s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
+                          (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
+            __stcs(gd + i * npad + d, Prec<P>::encode(gg[i], refs[Q + i]));
         }
     }
-}
-
-template <class R>
-Model<R> model_of(const ld_params& p) {
-    Model<R> m;
-    m.A = (R)p.A;
-    m.B = (R)p.B;
-    m.kappa = (R)p.kappa;
-    m.Gamma = (R)p.Gamma;
-    m.omega_f = (R)(1.0 / p.tau_f);
-    m.omega_g = (R)(1.0 / p.tau_g);
-    m.force_pre = (R)(1.0 - 0.5 / p.tau_f);
-    return m;
 }
 
 constexpr int kTY = 8;
@@ -186,18 +172,8 @@ cudaError_t step_fused_p(ld_ctx* c) {
 
 }  // namespace
 
-bool fused_supported(int nx, int ny, int nz) {
+inline bool fused_supported_impl(int nx, int ny, int nz) {
     return nx % kTX == 0 && ny % kTY == 0 && nz >= 4 && choose_zc(nx, ny, nz) > 0;
-}
-
-cudaError_t launch_step_fused(ld_ctx* c) {
-    switch (c->prec) {
-        case LD_FP64: return step_fused_p<LD_FP64>(c);
-        case LD_FP32: return step_fused_p<LD_FP32>(c);
-        case LD_FP16DEV: return step_fused_p<LD_FP16DEV>(c);
-        case LD_BF16DEV: return step_fused_p<LD_BF16DEV>(c);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 }  // namespace ld

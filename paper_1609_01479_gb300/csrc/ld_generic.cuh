@@ -2,7 +2,9 @@
 // site. The step runs as three launches -- phi (zeroth moment of g),
 // mu (7-point stencil), and collide+propagate -- and the same file holds the
 // initialiser, the macroscopic output, the FP64 conservation sums, the
-// codec I/O and propagation alone.
+// codec I/O and propagation alone. Templates only: instantiated per storage
+// precision by ld_prec_f64.cu and ld_prec_lp.cu.
+#pragma once
 #include "ld_common.cuh"
 #include "ld_internal.h"
 
@@ -29,19 +31,6 @@ __device__ __forceinline__ long long site_of(const Geom& g, int x, int y, int z)
 // Coordinate after a displacement of -1, 0 or +1 (periodic).
 __device__ __forceinline__ int step_coord(int a, int d, int n) {
     return d > 0 ? wrap_inc(a, n) : (d < 0 ? wrap_dec(a, n) : a);
-}
-
-template <class R>
-Model<R> model_of(const ld_params& p) {
-    Model<R> m;
-    m.A = (R)p.A;
-    m.B = (R)p.B;
-    m.kappa = (R)p.kappa;
-    m.Gamma = (R)p.Gamma;
-    m.omega_f = (R)(1.0 / p.tau_f);
-    m.omega_g = (R)(1.0 / p.tau_g);
-    m.force_pre = (R)(1.0 - 0.5 / p.tau_f);
-    return m;
 }
 
 // ---------------------------------------------------------------------------
@@ -104,9 +93,7 @@ __global__ void __launch_bounds__(kThreads)
     for (int i = 0; i < Q; ++i) {
         f[i] = Prec<P>::decode(fs[i * g.npad + s], ref[i]);
         rho += f[i];
-        jx += R(cx(i)) * f[i];
-        jy += R(cy(i)) * f[i];
-        jz += R(cz(i)) * f[i];
+        add_c(i, f[i], jx, jy, jz);
     }
     R ux, uy, uz;
     guo_velocity(rho, jx, jy, jz, Fx, Fy, Fz, ux, uy, uz);
@@ -424,35 +411,14 @@ cudaError_t encode_p(ld_ctx* c, const double* f, const double* gin) {
     return cudaGetLastError();
 }
 
-}  // namespace
 
-#define LD_DISPATCH(fn, ...)                                        \
-    switch (c->prec) {                                              \
-        case LD_FP64: return fn<LD_FP64>(__VA_ARGS__);              \
-        case LD_FP32: return fn<LD_FP32>(__VA_ARGS__);              \
-        case LD_FP16DEV: return fn<LD_FP16DEV>(__VA_ARGS__);        \
-        case LD_BF16DEV: return fn<LD_BF16DEV>(__VA_ARGS__);        \
-        default: return cudaErrorInvalidValue;                      \
-    }
-
-cudaError_t launch_init(ld_ctx* c, const double* phi, const double* rho, const double* u) {
-    LD_DISPATCH(init_p, c, phi, rho, u);
-}
-cudaError_t launch_phi_mu(ld_ctx* c, int buf) { LD_DISPATCH(phi_mu_p, c, buf); }
-cudaError_t launch_collide_generic(ld_ctx* c) { LD_DISPATCH(collide_p, c); }
-cudaError_t launch_macros(ld_ctx* c, double* rho, double* u, double* phi, double* gphi) {
-    LD_DISPATCH(macros_p, c, rho, u, phi, gphi);
-}
-cudaError_t launch_totals(ld_ctx* c, double* totals) { LD_DISPATCH(totals_p, c, totals); }
-cudaError_t launch_decode(ld_ctx* c, double* f, double* g) { LD_DISPATCH(decode_p, c, f, g); }
-cudaError_t launch_encode(ld_ctx* c, const double* f, const double* g) { LD_DISPATCH(encode_p, c, f, g); }
-
-cudaError_t launch_default_refs(ld_ctx* c) {
+// Precision-independent launches.
+cudaError_t default_refs(ld_ctx* c) {
     k_default_refs<<<1, 32, 0, c->stream>>>(c->prm.rho0, c->ref);
     return cudaGetLastError();
 }
 
-cudaError_t launch_propagate(ld_ctx* c, int reverse) {
+cudaError_t propagate_raw(ld_ctx* c, int reverse) {
     const Geom g = to_dev(c->geom);
     const void* src = c->dist[c->cur];
     void* dst = c->dist[1 - c->cur];
@@ -475,4 +441,5 @@ cudaError_t launch_propagate(ld_ctx* c, int reverse) {
     return cudaGetLastError();
 }
 
+}  // namespace
 }  // namespace ld

@@ -1,0 +1,60 @@
+// FP32, FP16-deviation and BF16-deviation instantiations of the step
+// kernels, and the launches that do not depend on the precision.
+#include "ld_fused.cuh"
+#include "ld_generic.cuh"
+#include "ld_pipe.cuh"
+
+namespace ld {
+namespace lp {
+
+#define LD_LP_DISPATCH(fn, ...)                              \
+    switch (c->prec) {                                       \
+        case LD_FP32: return fn<LD_FP32>(__VA_ARGS__);       \
+        case LD_FP16DEV: return fn<LD_FP16DEV>(__VA_ARGS__); \
+        case LD_BF16DEV: return fn<LD_BF16DEV>(__VA_ARGS__); \
+        default: return cudaErrorInvalidValue;               \
+    }
+
+cudaError_t init(ld_ctx* c, const double* phi, const double* rho, const double* u) {
+    LD_LP_DISPATCH(init_p, c, phi, rho, u);
+}
+cudaError_t phi_mu(ld_ctx* c, int buf) { LD_LP_DISPATCH(phi_mu_p, c, buf); }
+cudaError_t collide_generic(ld_ctx* c) { LD_LP_DISPATCH(collide_p, c); }
+cudaError_t macros(ld_ctx* c, double* rho, double* u, double* phi, double* gphi) {
+    LD_LP_DISPATCH(macros_p, c, rho, u, phi, gphi);
+}
+cudaError_t totals(ld_ctx* c, double* t) { LD_LP_DISPATCH(totals_p, c, t); }
+cudaError_t decode(ld_ctx* c, double* f, double* g) { LD_LP_DISPATCH(decode_p, c, f, g); }
+cudaError_t encode(ld_ctx* c, const double* f, const double* g) { LD_LP_DISPATCH(encode_p, c, f, g); }
+cudaError_t step_fused_regs(ld_ctx* c) { LD_LP_DISPATCH(step_fused_p, c); }
+cudaError_t step_tma(ld_ctx* c) { LD_LP_DISPATCH(step_tma_p, c); }
+bool regs_supported(int nx, int ny, int nz) { return fused_supported_impl(nx, ny, nz); }
+bool tma_supported(int nx, int ny, int nz, int prec) {
+    switch (prec) {
+        case LD_FP32: return pipe_supported_p<LD_FP32>(nx, ny, nz);
+        case LD_FP16DEV: return pipe_supported_p<LD_FP16DEV>(nx, ny, nz);
+        case LD_BF16DEV: return pipe_supported_p<LD_BF16DEV>(nx, ny, nz);
+        default: return false;
+    }
+}
+
+#undef LD_LP_DISPATCH
+
+}  // namespace lp
+
+cudaError_t launch_propagate(ld_ctx* c, int reverse) { return propagate_raw(c, reverse); }
+cudaError_t launch_default_refs(ld_ctx* c) { return default_refs(c); }
+int choose_step_kernel(int nx, int ny, int nz, int prec, int requested) {
+    const bool f64p = prec == LD_FP64;
+    const bool tma = f64p ? f64::tma_supported(nx, ny, nz, prec) : lp::tma_supported(nx, ny, nz, prec);
+    const bool regs = f64p ? f64::regs_supported(nx, ny, nz) : lp::regs_supported(nx, ny, nz);
+    switch (requested) {
+        case LD_KERNEL_GENERIC: return kStepGeneric;
+        case LD_KERNEL_FUSED: return regs ? kStepRegs : 0;
+        case LD_KERNEL_FUSED_TMA: return tma ? kStepTma : 0;
+        case LD_KERNEL_AUTO: return regs ? kStepRegs : kStepGeneric;
+        default: return 0;
+    }
+}
+
+}  // namespace ld

@@ -20,11 +20,12 @@ import torch
 from . import build as _build
 
 LD_FP64, LD_FP32, LD_FP16DEV, LD_BF16DEV = 0, 1, 2, 3
-LD_KERNEL_AUTO, LD_KERNEL_GENERIC, LD_KERNEL_FUSED = 0, 1, 2
+LD_KERNEL_AUTO, LD_KERNEL_GENERIC, LD_KERNEL_FUSED, LD_KERNEL_FUSED_TMA = 0, 1, 2, 3
 LD_OK, LD_EINVAL, LD_ECUDA, LD_ENONFINITE, LD_ESTATE = 0, -1, -2, -3, -4
 
 PRECISIONS = {"fp64": LD_FP64, "fp32": LD_FP32, "fp16dev": LD_FP16DEV, "bf16dev": LD_BF16DEV}
-KERNELS = {"auto": LD_KERNEL_AUTO, "generic": LD_KERNEL_GENERIC, "fused": LD_KERNEL_FUSED}
+KERNELS = {"auto": LD_KERNEL_AUTO, "generic": LD_KERNEL_GENERIC, "fused": LD_KERNEL_FUSED,
+           "fused_tma": LD_KERNEL_FUSED_TMA}
 STORE_BYTES = {LD_FP64: 8, LD_FP32: 4, LD_FP16DEV: 2, LD_BF16DEV: 2}
 Q = 19
 

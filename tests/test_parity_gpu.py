@@ -61,10 +61,26 @@ def oracle_run(phi, steps, prm=None, rho=None, u=None):
     return m
 
 
-def assert_parity(gpu, ref, tol, fields=("rho", "u", "phi", "grad_phi", "f", "g")):
+def oracle_u_floor(phi, steps, prm=None, rho=None, u=None):
+    """Relative L2 change of the oracle's own u after `steps` steps when its
+    initial distributions move by at most one ulp: the rounding floor of u.
+    u = (j + F/2)/rho is a cancellation of O(w_i) values, so when |u| is small
+    this floor can exceed 1e-12 (7.7e-12 for the 16^3 spinodal at 100 steps)."""
+    prm = oracle.param_vector() if prm is None else prm
+    f, g = oracle.init(phi, prm, rho=rho, u=u)
+    rng = np.random.default_rng(1234)
+    fp = f + np.spacing(f) * rng.choice([-1.0, 0.0, 1.0], size=f.shape)
+    gp = g + np.spacing(g) * rng.choice([-1.0, 0.0, 1.0], size=g.shape)
+    a = oracle.macros(*oracle.step(f, g, prm, steps), prm)["u"]
+    b = oracle.macros(*oracle.step(fp, gp, prm, steps), prm)["u"]
+    return rel_l2(b, a)
+
+
+def assert_parity(gpu, ref, tol, fields=("rho", "u", "phi", "grad_phi", "f", "g"), u_tol=None):
     for k in fields:
         err = rel_l2(gpu[k], ref[k])
-        assert err <= tol, f"{k}: relative L2 {err:.3e} > {tol:.1e}"
+        t = u_tol if (k == "u" and u_tol is not None) else tol
+        assert err <= t, f"{k}: relative L2 {err:.3e} > {t:.1e}"
     # rho is dominated by its mean: compare the deviation too
     drho = rel_l2(gpu["rho"] - 1.0, ref["rho"] - 1.0)
     assert drho <= max(tol * 1e3, 1e-9), f"rho-1: {drho:.3e}"
@@ -73,8 +89,11 @@ def assert_parity(gpu, ref, tol, fields=("rho", "u", "phi", "grad_phi", "f", "g"
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("steps", [10, 100])
 def test_fp64_generic_16cube(ld, steps):
+    """The 16^3 spinodal start (configuration 1): 1e-12 on every field; u is
+    held to max(1e-12, 4 x its own rounding floor)."""
     phi = inputs.spinodal_phi(16, 16, 16, seed=1)
-    assert_parity(gpu_run(ld, phi, steps), oracle_run(phi, steps), FP64_TOL)
+    u_tol = max(FP64_TOL, 4.0 * oracle_u_floor(phi, steps))
+    assert_parity(gpu_run(ld, phi, steps), oracle_run(phi, steps), FP64_TOL, u_tol=u_tol)
 
 
 @pytest.mark.parametrize("shape", [(4, 4, 4), (7, 6, 5), (5, 9, 33), (12, 4, 20)])
@@ -203,7 +222,7 @@ def test_save_load_roundtrip(ld):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16dev", 1e-2), ("bf16dev", 1e-1)])
-@pytest.mark.parametrize("kernel", ["generic", "fused"])
+@pytest.mark.parametrize("kernel", ["generic", "fused", "fused_tma"])
 def test_reduced_precision_error(ld, precision, tol, kernel):
     nz, ny, nx = 32, 32, 32
     phi = inputs.spinodal_phi(nx, ny, nz, seed=2)
@@ -215,13 +234,39 @@ def test_reduced_precision_error(ld, precision, tol, kernel):
 
 
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
+@pytest.mark.parametrize("shape", [(4, 8, 32), (8, 16, 64), (12, 24, 96), (16, 48, 32)])
+def test_tma_kernel_matches_oracle_and_generic(ld, precision, shape):
+    """The TMA-staged fused kernel on lattices that exercise every periodic
+    edge of its copies: one tile across x (nx = 32) or y, edge tiles on both
+    sides, z-chunks whose halo planes wrap (nz = 4, 12). Same arithmetic as the
+    generic kernel up to FMA contraction; against the FP64 oracle within the
+    storage-precision bound."""
+    nz, ny, nx = shape
+    phi = inputs.spinodal_phi(nx, ny, nz, seed=13, amplitude=0.3)
+    steps = 15
+    a = gpu_run(ld, phi, steps, precision=precision, kernel="generic")
+    b = gpu_run(ld, phi, steps, precision=precision, kernel="fused_tma")
+    r = oracle_run(phi, steps)
+    tol = {"fp32": 1e-5, "fp16dev": 1e-2, "bf16dev": 1e-1}[precision]
+    assert rel_l2(b["phi"], r["phi"]) <= tol
+    # rho is stored as f_i ~ w_i rho: its deviation from 1 is not resolved
+    # beyond the storage ulp, so rho itself is compared
+    assert rel_l2(b["rho"], r["rho"]) <= tol
+    # generic and fused perform the same operations; only contraction differs
+    same = {"fp32": 1e-6, "fp16dev": 2e-3, "bf16dev": 2e-2}[precision]
+    assert rel_l2(b["phi"], a["phi"]) <= same
+    assert rel_l2(b["f"], a["f"]) <= same
+
+
 def test_generic_and_fused_agree(ld):
     nz, ny, nx = 8, 16, 64
     phi = inputs.spinodal_phi(nx, ny, nz, seed=12, amplitude=0.4)
     a = gpu_run(ld, phi, 30, precision="fp32", kernel="generic")
-    b = gpu_run(ld, phi, 30, precision="fp32", kernel="fused")
-    assert rel_l2(b["phi"], a["phi"]) < 1e-6
-    assert rel_l2(b["f"], a["f"]) < 1e-6
+    for kernel in ("fused", "fused_tma"):
+        b = gpu_run(ld, phi, 30, precision="fp32", kernel=kernel)
+        assert rel_l2(b["phi"], a["phi"]) < 1e-6
+        assert rel_l2(b["f"], a["f"]) < 1e-6
 
 
 def test_errors_are_reported_not_raised_on_device(ld):
