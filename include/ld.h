@@ -147,6 +147,22 @@ size_t ld_state_bytes(const ld_ctx* ctx);
 int ld_save_state(ld_ctx* ctx, void* dev_buf);
 int ld_load_state(ld_ctx* ctx, const void* dev_buf);
 
+/* FP64 totals {sum rho, sum phi, sum jx, sum jy, sum jz} of distributions
+ * given as device double[19][N] each (N = nx*ny*nz, the layout of
+ * ld_get_distributions), written to device totals[5], on cuda_stream.
+ * The paper has no counterpart to this call. It serves callers that cannot
+ * allocate device memory or provide a workspace -- e.g. a monitoring or
+ * checkpoint hook that must leave a running simulation's device-memory
+ * footprint unchanged, or code running inside another library's allocator
+ * callback: it allocates nothing, and keeps its partial sums in a fixed
+ * static device array (160 KiB, held by every GPU that loads the library
+ * until exit). Limit: N <= 67,108,864 sites (LD_EINVAL beyond). The first
+ * call on a device looks up that array's address and should come before any
+ * stream capture. Calls share the array: calls that overlap on the GPU race.
+ * Summation order is fixed (bitwise reproducible). No context needed;
+ * errors are read with ld_last_error(NULL). */
+int ld_totals_static(int nx, int ny, int nz, const double* f, const double* g, double* totals, void* cuda_stream);
+
 /* Message for an error code, and the last error recorded on a context. */
 const char* ld_strerror(int code);
 const char* ld_last_error(const ld_ctx* ctx);

@@ -113,6 +113,16 @@ int check_ready(ld_ctx* c) {
 
 namespace ld {
 size_t dist_bytes(const ld_ctx* c) { return 2 * kQ * (size_t)c->geom.npad * c->store_bytes; }
+
+int report_error(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+bool is_device_pointer(const void* p) { return is_device_ptr(p); }
 }  // namespace ld
 
 extern "C" {

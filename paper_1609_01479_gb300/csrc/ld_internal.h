@@ -48,6 +48,12 @@ struct ld_ctx {
 namespace ld {
 
 size_t dist_bytes(const ld_ctx* c);  // one buffer (f and g)
+
+// ld_api.cu: record a context-free error message (returned by
+// ld_last_error(NULL)) and return `code`; device-pointer test used by every
+// entry point.
+int report_error(int code, const char* fmt, ...);
+bool is_device_pointer(const void* p);
 inline void* f_of(const ld_ctx* c, int buf) { return c->dist[buf]; }
 inline void* g_of(const ld_ctx* c, int buf) {
     return static_cast<char*>(c->dist[buf]) + dist_bytes(c) / 2;

@@ -64,6 +64,7 @@ _SIGNATURES = {
     "ld_state_bytes": (ctypes.c_size_t, [_VP]),
     "ld_save_state": (ctypes.c_int, [_VP, _VP]),
     "ld_load_state": (ctypes.c_int, [_VP, _VP]),
+    "ld_totals_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "ld_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ld_last_error": (ctypes.c_char_p, [_VP]),
 }
@@ -180,6 +181,15 @@ def ld_save_state(ctx, buf):
 
 def ld_load_state(ctx, buf):
     return _call("ld_load_state", ctx, _ptr(buf))
+
+
+def ld_totals_static(nx, ny, nz, f, g, totals, stream=None):
+    """Allocation-free FP64 totals of double[19][N] distributions (see ld.h)."""
+    s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream(f.device).cuda_stream)
+    rc = lib().ld_totals_static(nx, ny, nz, _ptr(f), _ptr(g), _ptr(totals), s)
+    if rc != LD_OK:
+        raise LdError(rc, "ld_totals_static", lib().ld_last_error(None).decode(errors="replace"))
+    return rc
 
 
 def ld_strerror(code: int) -> str:
