@@ -53,6 +53,7 @@ def parse_args():
                     help="comma list; the first one is the primary line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -265,6 +266,66 @@ def time_e2e(args, ld, phi_host_pinned, precision):
     return ms, nbytes
 
 
+def time_adjoint(args, ld, phi_dev, precision, steps=20, every=5):
+    """Backward pass of a differentiable run on the bench lattice: seed, then
+    per segment (last first) recompute into a tape with ld_step_between and
+    run ld_adjoint_step over it in reverse, then ld_adjoint_init. Returns the
+    backward time per step, split into recompute and adjoint kernels, and the
+    forward time per step of the same run (plain ld_step)."""
+    import torch
+
+    n = args.size
+    stream = torch.cuda.current_stream()
+    sim = ld.LdSim(n, n, n, precision=precision, stream=stream.cuda_stream)
+    sim.init(phi_dev)
+    nbytes = ld.ld_state_bytes(sim.ctx)
+    ckpts = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(steps // every)]
+    tape = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(every - 1)]
+    adj_ws = torch.empty(ld.ld_adjoint_workspace_bytes(sim.ctx), dtype=torch.uint8, device="cuda")
+    ld.ld_adjoint_attach(sim.ctx, adj_ws)
+    grad = torch.zeros(2, dtype=torch.float64, device="cuda")
+    phibar = torch.empty_like(phi_dev).normal_()
+    gphi0 = torch.empty_like(phi_dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    # forward with checkpoints
+    f0, f1 = ev(), ev()
+    torch.cuda.synchronize()
+    f0.record(stream)
+    for c in ckpts:
+        ld.ld_save_state(sim.ctx, c)
+        ld.ld_step(sim.ctx, every)
+    f1.record(stream)
+    # backward
+    rec_ms = adj_ms = 0.0
+    b0 = ev()
+    b0.record(stream)
+    ld.ld_adjoint_seed(sim.ctx, phibar)
+    for c in reversed(ckpts):
+        r0, r1, a1 = ev(), ev(), ev()
+        r0.record(stream)
+        states = [c] + tape
+        for j in range(1, every):
+            ld.ld_step_between(sim.ctx, states[j - 1], states[j])
+        r1.record(stream)
+        for j in reversed(range(every)):
+            ld.ld_adjoint_step(sim.ctx, states[j], grad)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        rec_ms += r0.elapsed_time(r1)
+        adj_ms += r1.elapsed_time(a1)
+    ld.ld_adjoint_init(sim.ctx, phi_dev, gphi0, None, grad)
+    b1 = ev()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    out = {"steps": steps, "checkpoint_every": every, "forward_ms_per_step": f0.elapsed_time(f1) / steps,
+           "backward_ms_per_step": b0.elapsed_time(b1) / steps, "recompute_ms_per_step": rec_ms / steps,
+           "adjoint_kernels_ms_per_step": adj_ms / steps, "precision": precision}
+    sim.close()
+    del sim, ckpts, tape, adj_ws
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(sample_edge=96, sample_steps=20):
     """The FP64 oracle, as it stands, on the host cores: MLUPS on a bounded
     sample (a sample_edge^3 lattice of the same workload, sample_steps steps)."""
@@ -367,6 +428,7 @@ def main():
         e2e = {"value": world * n ** 3 * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
                "what": f"pinned phi0 H2D + ld_init + {args.steps} ld_step + ld_moments(phi) + D2H, one run"}
+    adj = None if args.no_adjoint else time_adjoint(args, ld, phi_dev, primary)
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline()
@@ -398,7 +460,8 @@ def main():
         "gpu_launches": args.steps + 2,
         "cpu_baseline": cpu,
         "per_precision": {p: {k: v for k, v in r.items() if k not in ("clocks",)} for p, r in results.items()},
-        "adjoint_forward_ratio": None,
+        "adjoint_forward_ratio": None if adj is None else adj["backward_ms_per_step"] / P["ms_per_step"],
+        "adjoint": adj,
     }
     print(json.dumps(line), flush=True)
 

@@ -147,6 +147,47 @@ size_t ld_state_bytes(const ld_ctx* ctx);
 int ld_save_state(ld_ctx* ctx, void* dev_buf);
 int ld_load_state(ld_ctx* ctx, const void* dev_buf);
 
+/* One full step from a saved state to another (both device buffers of
+ * ld_state_bytes() bytes, distinct), without touching the context's own
+ * state: used to recompute a checkpointed segment into a tape of states. */
+int ld_step_between(ld_ctx* ctx, const void* src_state, void* dst_state);
+
+/* ---- Adjoint (reverse mode) of the step above, the derivative of a scalar
+ * loss of the final phi with respect to the initial phi, kappa and tau_f.
+ * The paper has no adjoint; these calls are the exact transpose of the
+ * linearised step equations at the top of this file:
+ *   reverse propagation fbar*_i(x) = fbar_i(x + c_i) (and g), then the adjoint
+ *   of both collisions and of u = (j+F/2)/rho and F = -phi grad(mu), whose
+ *   non-local parts are the transposed central difference and the (symmetric)
+ *   7-point Laplacian; gbar_i = (1 - 1/tau_g) gbar*_i + phibar.
+ * The adjoint state is held in the arithmetic type (FP64 for LD_FP64,
+ * FP32 otherwise); parameter sums are FP64 in a fixed order. */
+
+/* Bytes of the adjoint workspace (two adjoint states, per-site scratch,
+ * per-block partials), and attaching one (device, 256-byte aligned). */
+size_t ld_adjoint_workspace_bytes(const ld_ctx* ctx);
+int ld_adjoint_attach(ld_ctx* ctx, void* dev_workspace, size_t bytes);
+
+/* Adjoint state at the final time T from dL/dphi_T (device double[N]):
+ * fbar = 0, gbar_i = dL/dphi_T (phi_T = sum_i g_i). */
+int ld_adjoint_seed(ld_ctx* ctx, const double* phibar);
+
+/* Map the adjoint state at t+1 to the one at t, given the forward state at
+ * time t (a device state buffer as written by ld_save_state or
+ * ld_step_between). Adds dL/dkappa and dL/dtau_f of this step into
+ * grad_params[0..1] (device doubles; NULL to skip). The context's current
+ * kappa and tau_f must be those of the forward run. */
+int ld_adjoint_step(ld_ctx* ctx, const void* state_t, double* grad_params);
+
+/* Adjoint of ld_init (rho = rho0 implied; u0 the initial velocity or NULL):
+ * writes dL/dphi0 (device double[N]) from the adjoint state at t = 0 and adds
+ * the initialiser's dL/dkappa into grad_params[0] (NULL to skip). */
+int ld_adjoint_init(ld_ctx* ctx, const double* phi0, const double* u0, double* grad_phi0, double* grad_params);
+
+/* Read or overwrite the current adjoint state as device double[19][N] each. */
+int ld_adjoint_get(ld_ctx* ctx, double* fbar, double* gbar);
+int ld_adjoint_set(ld_ctx* ctx, const double* fbar, const double* gbar);
+
 /* FP64 totals {sum rho, sum phi, sum jx, sum jy, sum jz} of distributions
  * given as device double[19][N] each (N = nx*ny*nz, the layout of
  * ld_get_distributions), written to device totals[5], on cuda_stream.

@@ -233,13 +233,7 @@ int ld_step(ld_ctx* c, int nsteps) {
     if (rc) return rc;
     if (nsteps < 0) return fail(c, LD_EINVAL, "nsteps must be >= 0");
     for (int t = 0; t < nsteps; ++t) {
-        cudaError_t e;
-        if (c->step_kernel != ld::kStepGeneric) {
-            e = ld::launch_step_fused(c);
-        } else {
-            e = ld::launch_phi_mu(c, c->cur);
-            if (e == cudaSuccess) e = ld::launch_collide_generic(c);
-        }
+        cudaError_t e = ld::launch_step(c, c->dist[c->cur], c->dist[1 - c->cur]);
         if (e != cudaSuccess) return cuda_fail(c, e, "ld_step");
         c->cur ^= 1;
     }
@@ -329,6 +323,125 @@ int ld_load_state(ld_ctx* c, const void* dev_buf) {
                             cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ld_load_state");
     c->initialized = true;
+    return LD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint
+
+}  // extern "C"
+
+namespace {
+struct AdjLayout {
+    size_t adj, gmb, mub, phib, part, total;
+};
+AdjLayout adj_layout_of(const ld_ctx* c) {
+    const size_t npad = (size_t)c->geom.npad;
+    const size_t rb = c->real_bytes;
+    const size_t nblk = (size_t)((c->geom.n + 255) / 256);
+    AdjLayout L;
+    size_t off = 0;
+    L.adj = off;
+    off += 2 * align_up(2 * kQ * npad * rb);
+    L.gmb = off;
+    off += align_up(3 * npad * rb);
+    L.mub = off;
+    off += align_up(npad * rb);
+    L.phib = off;
+    off += align_up(npad * rb);
+    L.part = off;
+    off += align_up(2 * nblk * sizeof(double));
+    L.total = off;
+    return L;
+}
+int check_adj(ld_ctx* c) {
+    if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
+    if (!c->adj_ready) return fail(c, LD_ESTATE, "no adjoint workspace attached (call ld_adjoint_attach)");
+    return LD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+size_t ld_adjoint_workspace_bytes(const ld_ctx* c) { return c ? adj_layout_of(c).total : 0; }
+
+int ld_adjoint_attach(ld_ctx* c, void* dev_workspace, size_t bytes) {
+    if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
+    const AdjLayout L = adj_layout_of(c);
+    if (!is_device_ptr(dev_workspace)) return fail(c, LD_EINVAL, "adjoint workspace is not a device pointer");
+    if ((uintptr_t)dev_workspace % kAlign) return fail(c, LD_EINVAL, "adjoint workspace must be 256-byte aligned");
+    if (bytes < L.total)
+        return fail(c, LD_EINVAL, "adjoint workspace of %zu bytes is smaller than the %zu needed", bytes, L.total);
+    char* w = (char*)dev_workspace;
+    const size_t one = align_up(2 * kQ * (size_t)c->geom.npad * c->real_bytes);
+    c->adj[0] = w + L.adj;
+    c->adj[1] = w + L.adj + one;
+    c->adj_gmb = w + L.gmb;
+    c->adj_mub = w + L.mub;
+    c->adj_phib = w + L.phib;
+    c->adj_part = (double*)(w + L.part);
+    c->adj_cur = 0;
+    c->adj_ready = true;
+    return LD_OK;
+}
+
+int ld_step_between(ld_ctx* c, const void* src_state, void* dst_state) {
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (!is_device_ptr(src_state) || !is_device_ptr(dst_state) || src_state == dst_state)
+        return fail(c, LD_EINVAL, "src and dst must be distinct device state buffers");
+    cudaError_t e = ld::launch_step(c, src_state, dst_state);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_step_between");
+    return LD_OK;
+}
+
+int ld_adjoint_seed(ld_ctx* c, const double* phibar) {
+    int rc = check_adj(c);
+    if (rc) return rc;
+    if (!is_device_ptr(phibar)) return fail(c, LD_EINVAL, "phibar must be a device pointer");
+    cudaError_t e = ld::launch_adj_seed(c, phibar);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_adjoint_seed");
+    return LD_OK;
+}
+
+int ld_adjoint_step(ld_ctx* c, const void* state_t, double* grad_params) {
+    int rc = check_adj(c);
+    if (rc) return rc;
+    if (!is_device_ptr(state_t)) return fail(c, LD_EINVAL, "state_t must be a device state buffer");
+    if (!opt_device(grad_params)) return fail(c, LD_EINVAL, "grad_params must be a device pointer or NULL");
+    cudaError_t e = ld::launch_adj_step(c, state_t, grad_params);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_adjoint_step");
+    c->adj_cur ^= 1;
+    return LD_OK;
+}
+
+int ld_adjoint_init(ld_ctx* c, const double* phi0, const double* u0, double* grad_phi0, double* grad_params) {
+    int rc = check_adj(c);
+    if (rc) return rc;
+    if (!is_device_ptr(phi0) || !is_device_ptr(grad_phi0))
+        return fail(c, LD_EINVAL, "phi0 and grad_phi0 must be device pointers");
+    if (!opt_device(u0) || !opt_device(grad_params))
+        return fail(c, LD_EINVAL, "u0 and grad_params must be device pointers or NULL");
+    cudaError_t e = ld::launch_adj_init(c, phi0, u0, grad_phi0, grad_params);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_adjoint_init");
+    return LD_OK;
+}
+
+int ld_adjoint_get(ld_ctx* c, double* fbar, double* gbar) {
+    int rc = check_adj(c);
+    if (rc) return rc;
+    if (!opt_device(fbar) || !opt_device(gbar)) return fail(c, LD_EINVAL, "outputs must be device pointers or NULL");
+    cudaError_t e = ld::launch_adj_io(c, 1, fbar, gbar);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_adjoint_get");
+    return LD_OK;
+}
+
+int ld_adjoint_set(ld_ctx* c, const double* fbar, const double* gbar) {
+    int rc = check_adj(c);
+    if (rc) return rc;
+    if (!is_device_ptr(fbar) || !is_device_ptr(gbar)) return fail(c, LD_EINVAL, "fbar and gbar must be device pointers");
+    cudaError_t e = ld::launch_adj_io(c, 0, const_cast<double*>(fbar), const_cast<double*>(gbar));
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_adjoint_set");
     return LD_OK;
 }
 

@@ -157,15 +157,15 @@ int choose_zc(int nx, int ny, int nz) {
 }
 
 template <int P>
-cudaError_t step_fused_p(ld_ctx* c) {
+cudaError_t step_fused_p(ld_ctx* c, const void* src, void* dst) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
     const int zc = choose_zc(g.nx, g.ny, g.nz);
     const dim3 grid(g.nx / kTX, g.ny / kTY, g.nz / zc);
-    const int a = c->cur, b = 1 - c->cur;
-    k_step_fused<P, kTY><<<grid, kTX * kTY, 0, c->stream>>>(g, model_of<R>(c->prm), zc, (const S*)f_of(c, a),
-                                                            (const S*)g_of(c, a), (S*)f_of(c, b), (S*)g_of(c, b),
+    k_step_fused<P, kTY><<<grid, kTX * kTY, 0, c->stream>>>(g, model_of<R>(c->prm), zc, (const S*)f_part(c, src),
+                                                            (const S*)g_part(c, src), (S*)f_part(c, dst),
+                                                            (S*)g_part(c, dst),
                                                             c->ref);
     return cudaGetLastError();
 }

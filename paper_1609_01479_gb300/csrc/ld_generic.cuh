@@ -348,24 +348,23 @@ cudaError_t init_p(ld_ctx* c, const double* phi, const double* rho, const double
 }
 
 template <int P>
-cudaError_t phi_mu_p(ld_ctx* c, int buf) {
+cudaError_t phi_mu_p(ld_ctx* c, const void* state) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     const Geom g = to_dev(c->geom);
-    k_phi<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, (const S*)g_of(c, buf), c->ref, (R*)c->phi);
+    k_phi<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, (const S*)g_part(c, state), c->ref, (R*)c->phi);
     k_mu<R><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, model_of<R>(c->prm), (const R*)c->phi, (R*)c->mu);
     return cudaGetLastError();
 }
 
 template <int P>
-cudaError_t collide_p(ld_ctx* c) {
+cudaError_t collide_p(ld_ctx* c, const void* src, void* dst) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     const Geom g = to_dev(c->geom);
-    const int a = c->cur, b = 1 - c->cur;
     k_collide<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(
-        g, model_of<R>(c->prm), (const S*)f_of(c, a), (const S*)g_of(c, a), (S*)f_of(c, b), (S*)g_of(c, b),
-        (const R*)c->phi, (const R*)c->mu, c->ref);
+        g, model_of<R>(c->prm), (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
+        (S*)g_part(c, dst), (const R*)c->phi, (const R*)c->mu, c->ref);
     return cudaGetLastError();
 }
 
@@ -374,7 +373,7 @@ cudaError_t macros_p(ld_ctx* c, double* rho, double* u, double* phi, double* gph
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     const Geom g = to_dev(c->geom);
-    cudaError_t e = phi_mu_p<P>(c, c->cur);
+    cudaError_t e = phi_mu_p<P>(c, c->dist[c->cur]);
     if (e != cudaSuccess) return e;
     k_macros<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, (const S*)f_of(c, c->cur), (const S*)g_of(c, c->cur),
                                                              (const R*)c->phi, (const R*)c->mu, c->ref, rho, u,

@@ -41,6 +41,16 @@ struct ld_ctx {
     cudaStream_t stream;
     bool initialized;
     int step_kernel;  // ld::StepKernel
+    // adjoint (attached with ld_adjoint_attach): two adjoint states
+    // fbar[19][npad] + gbar[19][npad] in the arithmetic type, per-site scratch,
+    // per-block FP64 partials (2 per block)
+    bool adj_ready;
+    int adj_cur;
+    void* adj[2];
+    void* adj_gmb;   // 3 x npad
+    void* adj_mub;   // npad
+    void* adj_phib;  // npad
+    double* adj_part;
     int num_sms;      // multiprocessors of the current device
     char last_error[256];
 };
@@ -54,10 +64,14 @@ size_t dist_bytes(const ld_ctx* c);  // one buffer (f and g)
 // entry point.
 int report_error(int code, const char* fmt, ...);
 bool is_device_pointer(const void* p);
-inline void* f_of(const ld_ctx* c, int buf) { return c->dist[buf]; }
-inline void* g_of(const ld_ctx* c, int buf) {
-    return static_cast<char*>(c->dist[buf]) + dist_bytes(c) / 2;
+// A state buffer (a ping-pong buffer or a saved state) holds f[19][npad]
+// then g[19][npad] in the storage precision.
+inline void* f_part(const ld_ctx*, const void* state) { return const_cast<void*>(state); }
+inline void* g_part(const ld_ctx* c, const void* state) {
+    return static_cast<char*>(const_cast<void*>(state)) + dist_bytes(c) / 2;
 }
+inline void* f_of(const ld_ctx* c, int buf) { return f_part(c, c->dist[buf]); }
+inline void* g_of(const ld_ctx* c, int buf) { return g_part(c, c->dist[buf]); }
 
 // Launchers per storage precision. The FP64 set (ld_prec_f64.cu) is compiled
 // without fused multiply-add contraction so that its roundings follow the
@@ -66,14 +80,18 @@ inline void* g_of(const ld_ctx* c, int buf) {
 #define LD_PRECISION_LAUNCHERS(NS)                                                                \
     namespace NS {                                                                                \
     cudaError_t init(ld_ctx* c, const double* phi, const double* rho, const double* u);          \
-    cudaError_t phi_mu(ld_ctx* c, int buf);                                                       \
-    cudaError_t collide_generic(ld_ctx* c);                                                       \
+    cudaError_t phi_mu(ld_ctx* c, const void* state);                                             \
+    cudaError_t collide_generic(ld_ctx* c, const void* src, void* dst);                           \
     cudaError_t macros(ld_ctx* c, double* rho, double* u, double* phi, double* grad_phi);         \
     cudaError_t totals(ld_ctx* c, double* totals);                                                \
     cudaError_t decode(ld_ctx* c, double* f, double* g);                                          \
     cudaError_t encode(ld_ctx* c, const double* f, const double* g);                              \
-    cudaError_t step_fused_regs(ld_ctx* c);                                                       \
-    cudaError_t step_tma(ld_ctx* c);                                                              \
+    cudaError_t step_fused_regs(ld_ctx* c, const void* src, void* dst);                           \
+    cudaError_t step_tma(ld_ctx* c, const void* src, void* dst);                                  \
+    cudaError_t adj_step(ld_ctx* c, const void* state_t, double* grad);                           \
+    cudaError_t adj_seed(ld_ctx* c, const double* phibar);                                        \
+    cudaError_t adj_init(ld_ctx* c, const double* phi0, const double* u0, double* gphi0, double* grad); \
+    cudaError_t adj_io(ld_ctx* c, int to_double, double* fbar, double* gbar);                     \
     bool regs_supported(int nx, int ny, int nz);                                                  \
     bool tma_supported(int nx, int ny, int nz, int prec);                                         \
     }
@@ -95,9 +113,8 @@ inline bool is_f64(const ld_ctx* c) { return c->prec == LD_FP64; }
 inline cudaError_t launch_init(ld_ctx* c, const double* phi, const double* rho, const double* u) {
     return is_f64(c) ? f64::init(c, phi, rho, u) : lp::init(c, phi, rho, u);
 }
-inline cudaError_t launch_phi_mu(ld_ctx* c, int buf) { return is_f64(c) ? f64::phi_mu(c, buf) : lp::phi_mu(c, buf); }
-inline cudaError_t launch_collide_generic(ld_ctx* c) {
-    return is_f64(c) ? f64::collide_generic(c) : lp::collide_generic(c);
+inline cudaError_t launch_phi_mu(ld_ctx* c, const void* state) {
+    return is_f64(c) ? f64::phi_mu(c, state) : lp::phi_mu(c, state);
 }
 inline cudaError_t launch_macros(ld_ctx* c, double* rho, double* u, double* phi, double* gphi) {
     return is_f64(c) ? f64::macros(c, rho, u, phi, gphi) : lp::macros(c, rho, u, phi, gphi);
@@ -109,9 +126,29 @@ inline cudaError_t launch_decode(ld_ctx* c, double* f, double* g) {
 inline cudaError_t launch_encode(ld_ctx* c, const double* f, const double* g) {
     return is_f64(c) ? f64::encode(c, f, g) : lp::encode(c, f, g);
 }
-inline cudaError_t launch_step_fused(ld_ctx* c) {
-    if (c->step_kernel == kStepTma) return is_f64(c) ? f64::step_tma(c) : lp::step_tma(c);
-    return is_f64(c) ? f64::step_fused_regs(c) : lp::step_fused_regs(c);
+inline cudaError_t launch_adj_step(ld_ctx* c, const void* st, double* grad) {
+    return is_f64(c) ? f64::adj_step(c, st, grad) : lp::adj_step(c, st, grad);
+}
+inline cudaError_t launch_adj_seed(ld_ctx* c, const double* pb) {
+    return is_f64(c) ? f64::adj_seed(c, pb) : lp::adj_seed(c, pb);
+}
+inline cudaError_t launch_adj_init(ld_ctx* c, const double* phi0, const double* u0, double* gphi0, double* grad) {
+    return is_f64(c) ? f64::adj_init(c, phi0, u0, gphi0, grad) : lp::adj_init(c, phi0, u0, gphi0, grad);
+}
+inline cudaError_t launch_adj_io(ld_ctx* c, int to_double, double* fbar, double* gbar) {
+    return is_f64(c) ? f64::adj_io(c, to_double, fbar, gbar) : lp::adj_io(c, to_double, fbar, gbar);
+}
+
+// One full step from the state in `src` to the state in `dst` (distinct
+// buffers) with the context's step kernel.
+inline cudaError_t launch_step(ld_ctx* c, const void* src, void* dst) {
+    if (c->step_kernel == kStepGeneric) {
+        cudaError_t e = launch_phi_mu(c, src);
+        if (e != cudaSuccess) return e;
+        return is_f64(c) ? f64::collide_generic(c, src, dst) : lp::collide_generic(c, src, dst);
+    }
+    if (c->step_kernel == kStepTma) return is_f64(c) ? f64::step_tma(c, src, dst) : lp::step_tma(c, src, dst);
+    return is_f64(c) ? f64::step_fused_regs(c, src, dst) : lp::step_fused_regs(c, src, dst);
 }
 
 }  // namespace ld

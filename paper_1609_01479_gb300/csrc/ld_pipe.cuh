@@ -305,7 +305,7 @@ bool pipe_supported_p(int nx, int ny, int nz) {
 }
 
 template <int P>
-cudaError_t step_tma_p(ld_ctx* c) {
+cudaError_t step_tma_p(ld_ctx* c, const void* src, void* dst) {
     using L = PipeLayout<P>;
     using S = typename L::S;
     using R = typename L::R;
@@ -318,9 +318,9 @@ cudaError_t step_tma_p(ld_ctx* c) {
     const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
     const int zc = pipe_zc((g.nx / L::TX) * (g.ny / L::TY), g.nz, 2 * c->num_sms);  // two CTAs per SM
     const dim3 grid(g.nx / L::TX, g.ny / L::TY, g.nz / zc);
-    const int a = c->cur, b = 1 - c->cur;
-    k_step_tma<P><<<grid, L::NT, L::BYTES, c->stream>>>(g, model_of<R>(c->prm), zc, (const S*)f_of(c, a),
-                                                        (const S*)g_of(c, a), (S*)f_of(c, b), (S*)g_of(c, b), c->ref,
+    k_step_tma<P><<<grid, L::NT, L::BYTES, c->stream>>>(g, model_of<R>(c->prm), zc, (const S*)f_part(c, src),
+                                                        (const S*)g_part(c, src), (S*)f_part(c, dst),
+                                                        (S*)g_part(c, dst), c->ref,
                                                         c->status);
     return cudaGetLastError();
 }

@@ -64,6 +64,14 @@ _SIGNATURES = {
     "ld_state_bytes": (ctypes.c_size_t, [_VP]),
     "ld_save_state": (ctypes.c_int, [_VP, _VP]),
     "ld_load_state": (ctypes.c_int, [_VP, _VP]),
+    "ld_step_between": (ctypes.c_int, [_VP, _VP, _VP]),
+    "ld_adjoint_workspace_bytes": (ctypes.c_size_t, [_VP]),
+    "ld_adjoint_attach": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    "ld_adjoint_seed": (ctypes.c_int, [_VP, _VP]),
+    "ld_adjoint_step": (ctypes.c_int, [_VP, _VP, _VP]),
+    "ld_adjoint_init": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "ld_adjoint_get": (ctypes.c_int, [_VP, _VP, _VP]),
+    "ld_adjoint_set": (ctypes.c_int, [_VP, _VP, _VP]),
     "ld_totals_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "ld_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ld_last_error": (ctypes.c_char_p, [_VP]),
@@ -181,6 +189,38 @@ def ld_save_state(ctx, buf):
 
 def ld_load_state(ctx, buf):
     return _call("ld_load_state", ctx, _ptr(buf))
+
+
+def ld_step_between(ctx, src_state, dst_state):
+    return _call("ld_step_between", ctx, _ptr(src_state), _ptr(dst_state))
+
+
+def ld_adjoint_workspace_bytes(ctx) -> int:
+    return int(lib().ld_adjoint_workspace_bytes(ctx))
+
+
+def ld_adjoint_attach(ctx, workspace):
+    return _call("ld_adjoint_attach", ctx, _ptr(workspace), workspace.numel() * workspace.element_size())
+
+
+def ld_adjoint_seed(ctx, phibar):
+    return _call("ld_adjoint_seed", ctx, _ptr(phibar))
+
+
+def ld_adjoint_step(ctx, state_t, grad_params=None):
+    return _call("ld_adjoint_step", ctx, _ptr(state_t), _ptr(grad_params))
+
+
+def ld_adjoint_init(ctx, phi0, grad_phi0, u0=None, grad_params=None):
+    return _call("ld_adjoint_init", ctx, _ptr(phi0), _ptr(u0), _ptr(grad_phi0), _ptr(grad_params))
+
+
+def ld_adjoint_get(ctx, fbar=None, gbar=None):
+    return _call("ld_adjoint_get", ctx, _ptr(fbar), _ptr(gbar))
+
+
+def ld_adjoint_set(ctx, fbar, gbar):
+    return _call("ld_adjoint_set", ctx, _ptr(fbar), _ptr(gbar))
 
 
 def ld_totals_static(nx, ny, nz, f, g, totals, stream=None):

@@ -1,0 +1,200 @@
+"""Adjoint of the step (reverse mode, through the C ABI and LdRun) against
+the FP64 oracle's tangent-linear model and central finite differences.
+
+L = sum (phi_T - phi_target)^2. For a direction d = (dphi0, dkappa, dtau_f)
+the reverse-mode gradient must satisfy <grad L, d> = dL/d(eps) of the
+oracle's dual-number run (dot-product test); FP64 contexts to 1e-9, FP32
+to 1e-4 (the bound stated for the FP32 adjoint). Every component of dL/dphi0
+is also checked by central differences of the oracle at 8^3.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1609_01479_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_01479_gb300 import adjoint, ld
+
+    ld.lib()
+    return ld, adjoint
+
+
+def gpu_grads(adjoint, phi0, target, kappa, tau_f, spec):
+    p0 = torch.from_numpy(phi0).cuda().requires_grad_(True)
+    k = torch.tensor(kappa, dtype=torch.float64, requires_grad=True)
+    t = torch.tensor(tau_f, dtype=torch.float64, requires_grad=True)
+    phi_t = adjoint.run(p0, k, t, spec)
+    loss = ((phi_t - torch.from_numpy(target).cuda()) ** 2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    return float(loss.item()), p0.grad.cpu().numpy(), float(k.grad.item()), float(t.grad.item())
+
+
+def oracle_prm(kappa, tau_f, tau_g=1.0):
+    return oracle.param_vector(kappa=kappa, tau_f=tau_f, tau_g=tau_g)
+
+
+def target_phi(phi0, kappa_t, tau_f, steps):
+    prm = oracle_prm(kappa_t, tau_f)
+    f, g = oracle.init(phi0, prm)
+    f, g = oracle.step(f, g, prm, steps)
+    return g.sum(axis=0)
+
+
+@pytest.mark.parametrize("shape,steps,K,kernel", [((5, 6, 7), 12, 5, "generic"), ((4, 8, 32), 9, 4, "fused")])
+def test_dot_product_fp64(mods, shape, steps, K, kernel):
+    ld, adjoint = mods
+    nz, ny, nx = shape
+    phi0 = inputs.spinodal_phi(nx, ny, nz, seed=41, amplitude=0.3)
+    target = target_phi(phi0, 0.05, 0.9, steps)
+    kappa, tau_f = 0.04, 0.9
+    spec = adjoint.RunSpec(nx, ny, nz, steps, checkpoint_every=K, precision="fp64", kernel=kernel)
+    L, gphi, gk, gt = gpu_grads(adjoint, phi0, target, kappa, tau_f, spec)
+    prm = oracle_prm(kappa, tau_f)
+    assert L == pytest.approx(oracle.loss(phi0, target, prm, steps), rel=1e-11)
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        dphi = rng.standard_normal(phi0.shape)
+        dk, dt = rng.standard_normal(2)
+        dprm = np.zeros(7)
+        dprm[2], dprm[4] = dk, dt
+        _, dL = oracle.loss_jvp(phi0, target, prm, steps, dphi0=dphi, dprm=dprm)
+        ours = float((gphi * dphi).sum() + gk * dk + gt * dt)
+        assert ours == pytest.approx(dL, rel=1e-9, abs=1e-14)
+    # each parameter alone
+    for idx, g in ((2, gk), (4, gt)):
+        dprm = np.zeros(7)
+        dprm[idx] = 1.0
+        _, dL = oracle.loss_jvp(phi0, target, prm, steps, dprm=dprm)
+        assert g == pytest.approx(dL, rel=1e-9, abs=1e-14)
+
+
+def test_gradient_by_central_differences_8cube(mods):
+    """Every component of dL/dphi0, and dL/dkappa, dL/dtau_f, against central
+    differences of the FP64 oracle (h = 1e-6 relative)."""
+    ld, adjoint = mods
+    n, steps = 8, 10
+    phi0 = inputs.spinodal_phi(n, n, n, seed=42, amplitude=0.3)
+    target = target_phi(phi0, 0.05, 1.0, steps)
+    kappa, tau_f = 0.04, 1.0
+    spec = adjoint.RunSpec(n, n, n, steps, checkpoint_every=4, precision="fp64", kernel="generic")
+    L, gphi, gk, gt = gpu_grads(adjoint, phi0, target, kappa, tau_f, spec)
+    prm = oracle_prm(kappa, tau_f)
+    fd = np.zeros_like(phi0)
+    flat = phi0.reshape(-1)
+    for s in range(flat.size):
+        h = 1e-6 * max(1.0, abs(flat[s]))
+        p = flat.copy()
+        p[s] += h
+        lp = oracle.loss(p.reshape(phi0.shape), target, prm, steps)
+        p[s] -= 2 * h
+        lm = oracle.loss(p.reshape(phi0.shape), target, prm, steps)
+        fd.reshape(-1)[s] = (lp - lm) / (2 * h)
+    err = np.linalg.norm(gphi - fd) / np.linalg.norm(fd)
+    assert err < 1e-6, f"dL/dphi0 vs central differences: relative L2 {err:.2e}"
+    for idx, g, v in ((2, gk, kappa), (4, gt, tau_f)):
+        h = 1e-6 * v
+        pp, pm = prm.copy(), prm.copy()
+        pp[idx] += h
+        pm[idx] -= h
+        fdv = (oracle.loss(phi0, target, pp, steps) - oracle.loss(phi0, target, pm, steps)) / (2 * h)
+        assert g == pytest.approx(fdv, rel=1e-6)
+
+
+@pytest.mark.parametrize("kernel", ["fused", "generic"])
+def test_dot_product_fp32(mods, kernel):
+    """FP32 storage and FP32 adjoint arithmetic against the FP64 oracle:
+    dL/dphi0 (along a random direction) and dL/dkappa within 1e-4.
+    dL/dtau_f acts on phi only through the flow u = (j + F/2)/rho, and j is a
+    cancellation of O(w_i) values: FP32 storage of f leaves u a relative
+    rounding error of order 2^-24 * sum|f_i| / |j| ~ 1e-3 at |u| ~ 1e-4, so
+    dL/dtau_f is held to 1e-3. The residual phi_T - target (kappa_target =
+    0.08) stays far above the FP32 error of phi_T."""
+    ld, adjoint = mods
+    nz, ny, nx = 16, 16, 32
+    steps = 60
+    phi0 = inputs.spinodal_phi(nx, ny, nz, seed=43)
+    target = target_phi(phi0, 0.08, 1.0, steps)
+    spec = adjoint.RunSpec(nx, ny, nz, steps, checkpoint_every=10, precision="fp32", kernel=kernel)
+    L, gphi, gk, gt = gpu_grads(adjoint, phi0, target, 0.04, 1.0, spec)
+    prm = oracle_prm(0.04, 1.0)
+    rng = np.random.default_rng(8)
+    dphi = rng.standard_normal(phi0.shape)
+    _, dL = oracle.loss_jvp(phi0, target, prm, steps, dphi0=dphi)
+    assert float((gphi * dphi).sum()) == pytest.approx(dL, rel=1e-4)
+    errs = {}
+    for name, idx, g in (("kappa", 2, gk), ("tau_f", 4, gt)):
+        dprm = np.zeros(7)
+        dprm[idx] = 1.0
+        _, dL = oracle.loss_jvp(phi0, target, prm, steps, dprm=dprm)
+        errs[name] = abs(g - dL) / abs(dL)
+    assert errs["kappa"] <= 1e-4 and errs["tau_f"] <= 1e-3, errs
+
+
+def test_zero_loss_gives_zero_gradient(mods):
+    """At kappa = kappa_target the loss and every gradient vanish exactly."""
+    ld, adjoint = mods
+    nz, ny, nx = 8, 8, 32
+    steps = 6
+    phi0 = inputs.spinodal_phi(nx, ny, nz, seed=44)
+    spec = adjoint.RunSpec(nx, ny, nz, steps, checkpoint_every=4, precision="fp32")
+    p0 = torch.from_numpy(phi0).cuda()
+    k = torch.tensor(0.05, dtype=torch.float64)
+    t = torch.tensor(1.0, dtype=torch.float64)
+    target = adjoint.run(p0, k, t, spec).detach()
+    L, gphi, gk, gt = gpu_grads(adjoint, phi0, target.cpu().numpy(), 0.05, 1.0, spec)
+    assert L == 0.0 and gk == 0.0 and gt == 0.0
+    assert np.all(gphi == 0.0)
+
+
+def test_checkpoint_interval_does_not_change_gradients(mods):
+    """Recomputation reproduces the forward states bit for bit, so the
+    gradients do not depend on the checkpoint interval."""
+    ld, adjoint = mods
+    nz, ny, nx = 8, 8, 32
+    steps = 11
+    phi0 = inputs.spinodal_phi(nx, ny, nz, seed=45)
+    target = target_phi(phi0, 0.05, 1.0, steps)
+    res = []
+    for K in (1, 3, 11):
+        spec = adjoint.RunSpec(nx, ny, nz, steps, checkpoint_every=K, precision="fp32")
+        res.append(gpu_grads(adjoint, phi0, target, 0.04, 1.0, spec))
+    for r in res[1:]:
+        assert r[0] == res[0][0]
+        assert np.array_equal(r[1], res[0][1])
+        assert r[2] == res[0][2] and r[3] == res[0][3]
+
+
+@pytest.mark.slow
+def test_differentiable_run_64cube_200_steps(mods):
+    """The differentiable-run configuration: 64^3, 200 steps, FP32, checkpoint
+    every 20; target from a seeded run at kappa = 0.05; gradients along a
+    direction supported on an 8^3 sub-block, and for kappa and tau_f, against
+    the FP64 oracle's tangent-linear model (1e-4)."""
+    ld, adjoint = mods
+    n, steps = 64, 200
+    phi0 = inputs.spinodal_phi(n, n, n, seed=4)
+    target = target_phi(phi0, 0.05, 1.0, steps)
+    spec = adjoint.RunSpec(n, n, n, steps, checkpoint_every=20, precision="fp32")
+    L, gphi, gk, gt = gpu_grads(adjoint, phi0, target, 0.04, 1.0, spec)
+    prm = oracle_prm(0.04, 1.0)
+    rng = np.random.default_rng(9)
+    dphi = np.zeros_like(phi0)
+    dphi[28:36, 28:36, 28:36] = rng.standard_normal((8, 8, 8))
+    dprm = np.zeros(7)
+    dprm[2], dprm[4] = 0.5, -0.3
+    Lo, dL = oracle.loss_jvp(phi0, target, prm, steps, dphi0=dphi, dprm=dprm)
+    assert L == pytest.approx(Lo, rel=1e-4)
+    ours = float((gphi * dphi).sum() + 0.5 * gk - 0.3 * gt)
+    assert ours == pytest.approx(dL, rel=1e-4)
