@@ -182,12 +182,14 @@ def barrier(world):
 
 
 def max_over_ranks(world, value):
+    """Largest value over all ranks (NCCL on the GPU, gloo on the host)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -266,7 +268,7 @@ def time_e2e(args, ld, phi_host_pinned, precision):
     return ms, nbytes
 
 
-def time_adjoint(args, ld, phi_dev, precision, steps=20, every=5):
+def time_adjoint(args, ld, phi_dev, precision, steps=40, every=10):
     """Backward pass of a differentiable run on the bench lattice: seed, then
     per segment (last first) recompute into a tape with ld_step_between and
     run ld_adjoint_step over it in reverse, then ld_adjoint_init. Returns the
@@ -281,6 +283,8 @@ def time_adjoint(args, ld, phi_dev, precision, steps=20, every=5):
     nbytes = ld.ld_state_bytes(sim.ctx)
     ckpts = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(steps // every)]
     tape = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(every - 1)]
+    fbytes = ld.ld_fields_bytes(sim.ctx)
+    fields = [torch.empty(fbytes, dtype=torch.uint8, device="cuda") for _ in range(every - 1)]
     adj_ws = torch.empty(ld.ld_adjoint_workspace_bytes(sim.ctx), dtype=torch.uint8, device="cuda")
     ld.ld_adjoint_attach(sim.ctx, adj_ws)
     grad = torch.zeros(2, dtype=torch.float64, device="cuda")
@@ -296,7 +300,7 @@ def time_adjoint(args, ld, phi_dev, precision, steps=20, every=5):
         ld.ld_step(sim.ctx, every)
     f1.record(stream)
     # backward
-    rec_ms = adj_ms = 0.0
+    marks = []
     b0 = ev()
     b0.record(stream)
     ld.ld_adjoint_seed(sim.ctx, phibar)
@@ -305,23 +309,23 @@ def time_adjoint(args, ld, phi_dev, precision, steps=20, every=5):
         r0.record(stream)
         states = [c] + tape
         for j in range(1, every):
-            ld.ld_step_between(sim.ctx, states[j - 1], states[j])
+            ld.ld_step_between(sim.ctx, states[j - 1], states[j], fields[j - 1])
         r1.record(stream)
         for j in reversed(range(every)):
-            ld.ld_adjoint_step(sim.ctx, states[j], grad)
+            ld.ld_adjoint_step(sim.ctx, states[j], grad, fields[j] if j < every - 1 else None)
         a1.record(stream)
-        torch.cuda.synchronize()
-        rec_ms += r0.elapsed_time(r1)
-        adj_ms += r1.elapsed_time(a1)
+        marks.append((r0, r1, a1))
     ld.ld_adjoint_init(sim.ctx, phi_dev, gphi0, None, grad)
     b1 = ev()
     b1.record(stream)
     torch.cuda.synchronize()
+    rec_ms = sum(r0.elapsed_time(r1) for r0, r1, _ in marks)
+    adj_ms = sum(r1.elapsed_time(a1) for _, r1, a1 in marks)
     out = {"steps": steps, "checkpoint_every": every, "forward_ms_per_step": f0.elapsed_time(f1) / steps,
            "backward_ms_per_step": b0.elapsed_time(b1) / steps, "recompute_ms_per_step": rec_ms / steps,
            "adjoint_kernels_ms_per_step": adj_ms / steps, "precision": precision}
     sim.close()
-    del sim, ckpts, tape, adj_ws
+    del sim, ckpts, tape, fields, adj_ws
     torch.cuda.empty_cache()
     return out
 

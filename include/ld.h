@@ -149,8 +149,12 @@ int ld_load_state(ld_ctx* ctx, const void* dev_buf);
 
 /* One full step from a saved state to another (both device buffers of
  * ld_state_bytes() bytes, distinct), without touching the context's own
- * state: used to recompute a checkpointed segment into a tape of states. */
-int ld_step_between(ld_ctx* ctx, const void* src_state, void* dst_state);
+ * state: used to recompute a checkpointed segment into a tape of states.
+ * fields_out (device, ld_fields_bytes(), or NULL) receives the phi and mu
+ * fields of the source state ([phi npad][mu npad] in the arithmetic type),
+ * which ld_adjoint_step can then reuse instead of recomputing them. */
+size_t ld_fields_bytes(const ld_ctx* ctx);
+int ld_step_between(ld_ctx* ctx, const void* src_state, void* dst_state, void* fields_out);
 
 /* ---- Adjoint (reverse mode) of the step above, the derivative of a scalar
  * loss of the final phi with respect to the initial phi, kappa and tau_f.
@@ -174,10 +178,11 @@ int ld_adjoint_seed(ld_ctx* ctx, const double* phibar);
 
 /* Map the adjoint state at t+1 to the one at t, given the forward state at
  * time t (a device state buffer as written by ld_save_state or
- * ld_step_between). Adds dL/dkappa and dL/dtau_f of this step into
+ * ld_step_between) and optionally its phi/mu fields from ld_step_between
+ * (NULL: computed here). Adds dL/dkappa and dL/dtau_f of this step into
  * grad_params[0..1] (device doubles; NULL to skip). The context's current
  * kappa and tau_f must be those of the forward run. */
-int ld_adjoint_step(ld_ctx* ctx, const void* state_t, double* grad_params);
+int ld_adjoint_step(ld_ctx* ctx, const void* state_t, const void* fields_t, double* grad_params);
 
 /* Adjoint of ld_init (rho = rho0 implied; u0 the initial velocity or NULL):
  * writes dL/dphi0 (device double[N]) from the adjoint state at t = 0 and adds

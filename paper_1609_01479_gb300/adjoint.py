@@ -5,11 +5,13 @@ the state is saved every ``spec.checkpoint_every`` steps (ld_save_state).
 Backward (reverse mode, all in the library's kernels):
   ld_adjoint_seed(dL/dphi_T); for each segment, last first: recompute its
   states from the segment's checkpoint into a tape (ld_step_between, which
-  writes each step's output straight into the next tape buffer), then
-  ld_adjoint_step over the tape in reverse; finally ld_adjoint_init gives
-  dL/dphi0. dL/dkappa and dL/dtau_f accumulate in FP64 on the device.
+  writes each step's output straight into the next tape buffer and the
+  phi/mu fields of its input into a fields buffer), then ld_adjoint_step over
+  the tape in reverse; finally ld_adjoint_init gives dL/dphi0. dL/dkappa and
+  dL/dtau_f accumulate in FP64 on the device.
 Memory: one checkpoint per segment plus a tape of checkpoint_every - 1
-states, each ld_state_bytes() bytes.
+states (ld_state_bytes() each) and checkpoint_every - 1 field buffers
+(ld_fields_bytes() each).
 """
 
 from __future__ import annotations
@@ -74,16 +76,18 @@ class LdRun(torch.autograd.Function):
         grad = torch.zeros(2, dtype=torch.float64, device=dev)
         ld.ld_adjoint_seed(sim.ctx, grad_phi_t.detach().to(dtype=torch.float64).contiguous())
         nbytes = ld.ld_state_bytes(sim.ctx)
-        tape = [torch.empty(nbytes, dtype=torch.uint8, device=dev)
-                for _ in range(max(0, min(spec.checkpoint_every, spec.steps) - 1))]
+        ntape = max(0, min(spec.checkpoint_every, spec.steps) - 1)
+        tape = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(ntape)]
+        fbytes = ld.ld_fields_bytes(sim.ctx)
+        fields = [torch.empty(fbytes, dtype=torch.uint8, device=dev) for _ in range(ntape)]
         for seg in reversed(range(len(ctx.checkpoints))):
             t0 = seg * spec.checkpoint_every
             k = min(spec.checkpoint_every, spec.steps - t0)
             states = [ctx.checkpoints[seg]] + tape[:k - 1]
             for j in range(1, k):
-                ld.ld_step_between(sim.ctx, states[j - 1], states[j])
+                ld.ld_step_between(sim.ctx, states[j - 1], states[j], fields[j - 1])
             for j in reversed(range(k)):
-                ld.ld_adjoint_step(sim.ctx, states[j], grad)
+                ld.ld_adjoint_step(sim.ctx, states[j], grad, fields[j] if j < k - 1 else None)
         grad_phi0 = torch.empty_like(ctx.phi0)
         ld.ld_adjoint_init(sim.ctx, ctx.phi0, grad_phi0, None, grad)
         (kd, kdev), (td, tdev) = ctx.param_meta

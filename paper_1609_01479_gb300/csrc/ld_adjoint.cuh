@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kAdjThreads)
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double omega_bar = 0.0;
     if (s < g.n) {
+        typename Prec<P>::real_t omega_site = 0;
         int x, y, z;
         site_coords(g, s, x, y, z);
         const int xp = wrap_inc(x, g.nx), xm = wrap_dec(x, g.nx);
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(kAdjThreads)
             const R feq = w * rho * base;
             const R src = w * (R(3) * (cF - uF) + R(9) * cu * cF);
             // f collision: f* = (1-w_f) f + w_f feq + pre S
-            omega_bar += (double)(fbs[i] * (feq - f[i] - R(0.5) * src));
+            omega_site += fbs[i] * (feq - f[i] - R(0.5) * src);
             const R feqb = m.omega_f * fbs[i];
             const R Sb = m.force_pre * fbs[i];
             rhob += feqb * w * base;
@@ -138,6 +139,7 @@ __global__ void __launch_bounds__(kAdjThreads)
         gmb[2 * g.npad + s] = -ph * Fbz;
         mub[s] = mub_l;
         phib[s] = phib_l;
+        omega_bar = (double)omega_site;
         // fbar at t: direct term + rho and j
 #pragma unroll
         for (int i = 0; i < Q; ++i)
@@ -326,20 +328,23 @@ AdjPtrs<P> adj_ptrs(ld_ctx* c, int in_buf) {
 }
 
 template <int P>
-cudaError_t adj_step_p(ld_ctx* c, const void* state_t, double* grad) {
+cudaError_t adj_step_p(ld_ctx* c, const void* state_t, const void* fields_t, double* grad) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     const Geom g = to_dev(c->geom);
-    cudaError_t e = phi_mu_p<P>(c, state_t);
-    if (e != cudaSuccess) return e;
+    if (!fields_t) {
+        cudaError_t e = phi_mu_p<P>(c, state_t);
+        if (e != cudaSuccess) return e;
+    }
+    const R* phi = fields_t ? (const R*)fields_t : (const R*)c->phi;
+    const R* mu = fields_t ? (const R*)fields_t + g.npad : (const R*)c->mu;
     const AdjPtrs<P> p = adj_ptrs<P>(c, c->adj_cur);
     const Model<R> m = model_of<R>(c->prm);
     const unsigned nb = blocks_for(g.n);
-    k_adj_local<P><<<nb, kAdjThreads, 0, c->stream>>>(g, m, (const S*)f_part(c, state_t), (const R*)c->phi,
-                                                      (const R*)c->mu, c->ref, p.fb1, p.gb1, p.fb0, p.gmb, p.mub,
-                                                      p.phib, c->adj_part);
-    k_adj_mu<R><<<nb, kAdjThreads, 0, c->stream>>>(g, (const R*)c->phi, p.gmb, p.mub, c->adj_part);
-    k_adj_g<R><<<nb, kAdjThreads, 0, c->stream>>>(g, m, (const R*)c->phi, p.mub, p.phib, p.gb1, p.gb0);
+    k_adj_local<P><<<nb, kAdjThreads, 0, c->stream>>>(g, m, (const S*)f_part(c, state_t), phi, mu, c->ref, p.fb1,
+                                                      p.gb1, p.fb0, p.gmb, p.mub, p.phib, c->adj_part);
+    k_adj_mu<R><<<nb, kAdjThreads, 0, c->stream>>>(g, phi, p.gmb, p.mub, c->adj_part);
+    k_adj_g<R><<<nb, kAdjThreads, 0, c->stream>>>(g, m, phi, p.mub, p.phib, p.gb1, p.gb0);
     if (grad)
         k_adj_finalize<<<1, kAdjThreads, 0, c->stream>>>(c->adj_part, nb, -1.0 / (c->prm.tau_f * c->prm.tau_f),
                                                          grad);

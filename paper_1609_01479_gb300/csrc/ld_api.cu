@@ -385,12 +385,15 @@ int ld_adjoint_attach(ld_ctx* c, void* dev_workspace, size_t bytes) {
     return LD_OK;
 }
 
-int ld_step_between(ld_ctx* c, const void* src_state, void* dst_state) {
+size_t ld_fields_bytes(const ld_ctx* c) { return c ? align_up(2 * (size_t)c->geom.npad * c->real_bytes) : 0; }
+
+int ld_step_between(ld_ctx* c, const void* src_state, void* dst_state, void* fields_out) {
     int rc = check_ready(c);
     if (rc) return rc;
     if (!is_device_ptr(src_state) || !is_device_ptr(dst_state) || src_state == dst_state)
         return fail(c, LD_EINVAL, "src and dst must be distinct device state buffers");
-    cudaError_t e = ld::launch_step(c, src_state, dst_state);
+    if (!opt_device(fields_out)) return fail(c, LD_EINVAL, "fields_out must be a device pointer or NULL");
+    cudaError_t e = ld::launch_step(c, src_state, dst_state, fields_out);
     if (e != cudaSuccess) return cuda_fail(c, e, "ld_step_between");
     return LD_OK;
 }
@@ -404,12 +407,13 @@ int ld_adjoint_seed(ld_ctx* c, const double* phibar) {
     return LD_OK;
 }
 
-int ld_adjoint_step(ld_ctx* c, const void* state_t, double* grad_params) {
+int ld_adjoint_step(ld_ctx* c, const void* state_t, const void* fields_t, double* grad_params) {
     int rc = check_adj(c);
     if (rc) return rc;
     if (!is_device_ptr(state_t)) return fail(c, LD_EINVAL, "state_t must be a device state buffer");
-    if (!opt_device(grad_params)) return fail(c, LD_EINVAL, "grad_params must be a device pointer or NULL");
-    cudaError_t e = ld::launch_adj_step(c, state_t, grad_params);
+    if (!opt_device(fields_t) || !opt_device(grad_params))
+        return fail(c, LD_EINVAL, "fields_t and grad_params must be device pointers or NULL");
+    cudaError_t e = ld::launch_adj_step(c, state_t, fields_t, grad_params);
     if (e != cudaSuccess) return cuda_fail(c, e, "ld_adjoint_step");
     c->adj_cur ^= 1;
     return LD_OK;

@@ -116,6 +116,24 @@ __device__ __forceinline__ int wrap_dec(int a, int n) { return a == 0 ? n - 1 : 
 // ---------------------------------------------------------------------------
 // Per-site physics (one site, registers only).
 
+// Explicitly rounded products and sums: the compiler may not contract these
+// into fused multiply-adds, so every kernel that forms mu gets the same bits.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+
+// mu = A phi + B phi^3 - kappa lap, with lap = (sum of the six neighbours'
+// phi) - 6 phi; operations in that order, each rounded once.
+template <class R>
+__device__ __forceinline__ R chem_potential(R phi, R nb_sum, const Model<R>& m) {
+    const R lap = sub_rn(nb_sum, mul_rn(R(6), phi));
+    const R cubic = mul_rn(mul_rn(mul_rn(m.B, phi), phi), phi);
+    return sub_rn(add_rn(mul_rn(m.A, phi), cubic), mul_rn(m.kappa, lap));
+}
+
 // c_i . (ax, ay, az) over the nonzero components of c_i only, in x, y, z
 // order. Equal, bit for bit, to the full three-term sum (adding a zero
 // product changes nothing) without the multiplies by 0 and +-1 that IEEE

@@ -32,7 +32,8 @@ __global__ void __launch_bounds__(kTX * TY, 2)
     k_step_fused(Geom g, Model<typename Prec<P>::real_t> m, int zc,
                  const typename Prec<P>::store_t* __restrict__ fs, const typename Prec<P>::store_t* __restrict__ gs,
                  typename Prec<P>::store_t* __restrict__ fd, typename Prec<P>::store_t* __restrict__ gd,
-                 const float* __restrict__ ref_g) {
+                 const float* __restrict__ ref_g, typename Prec<P>::real_t* __restrict__ phi_out,
+                 typename Prec<P>::real_t* __restrict__ mu_out) {
     using R = typename Prec<P>::real_t;
     constexpr int PW = kTX + 4, PH = TY + 4;  // phi ring plane
     constexpr int MW = kTX + 2, MH = TY + 2;  // mu ring plane
@@ -68,10 +69,9 @@ __global__ void __launch_bounds__(kTX * TY, 2)
         for (int idx = tid; idx < MW * MH; idx += NT) {
             const int mx = idx % MW, my = idx / MW;
             const int hx = mx + 1, hy = my + 1;
-            const R p = phis[mid][hy][hx];
-            const R lap = phis[mid][hy][hx + 1] + phis[mid][hy][hx - 1] + phis[mid][hy + 1][hx]
-                        + phis[mid][hy - 1][hx] + phis[hi][hy][hx] + phis[lo][hy][hx] - R(6) * p;
-            mus[slot][my][mx] = m.A * p + m.B * p * p * p - m.kappa * lap;
+            const R nb = phis[mid][hy][hx + 1] + phis[mid][hy][hx - 1] + phis[mid][hy + 1][hx]
+                       + phis[mid][hy - 1][hx] + phis[hi][hy][hx] + phis[lo][hy][hx];
+            mus[slot][my][mx] = chem_potential(phis[mid][hy][hx], nb, m);
         }
     };
     auto ps = [&](int zp) { return (zp - z0 + 2) % 3; };  // phi slot of plane zp (zp >= z0-2)
@@ -109,6 +109,10 @@ __global__ void __launch_bounds__(kTX * TY, 2)
         const R gmy = R(0.5) * (mus[mc][ty + 2][tx + 1] - mus[mc][ty][tx + 1]);
         const R gmz = R(0.5) * (mus[ms(k + 1)][ty + 1][tx + 1] - mus[ms(k - 1)][ty + 1][tx + 1]);
         const R Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
+        if (phi_out) {  // fields of the source state, for the adjoint
+            phi_out[s] = ph;
+            mu_out[s] = muc;
+        }
 
         R f[Q];
         R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
@@ -157,7 +161,7 @@ int choose_zc(int nx, int ny, int nz) {
 }
 
 template <int P>
-cudaError_t step_fused_p(ld_ctx* c, const void* src, void* dst) {
+cudaError_t step_fused_p(ld_ctx* c, const void* src, void* dst, void* fields) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
@@ -165,8 +169,9 @@ cudaError_t step_fused_p(ld_ctx* c, const void* src, void* dst) {
     const dim3 grid(g.nx / kTX, g.ny / kTY, g.nz / zc);
     k_step_fused<P, kTY><<<grid, kTX * kTY, 0, c->stream>>>(g, model_of<R>(c->prm), zc, (const S*)f_part(c, src),
                                                             (const S*)g_part(c, src), (S*)f_part(c, dst),
-                                                            (S*)g_part(c, dst),
-                                                            c->ref);
+                                                            (S*)g_part(c, dst), c->ref,
+                                                            fields ? (R*)fields : nullptr,
+                                                            fields ? (R*)fields + c->geom.npad : nullptr);
     return cudaGetLastError();
 }
 

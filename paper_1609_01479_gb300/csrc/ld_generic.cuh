@@ -56,12 +56,10 @@ __global__ void __launch_bounds__(kThreads) k_mu(Geom g, Model<R> m, const R* __
     if (s >= g.n) return;
     int x, y, z;
     site_coords(g, s, x, y, z);
-    const R p = phi[s];
-    const R lap = phi[site_of(g, wrap_inc(x, g.nx), y, z)] + phi[site_of(g, wrap_dec(x, g.nx), y, z)]
-                + phi[site_of(g, x, wrap_inc(y, g.ny), z)] + phi[site_of(g, x, wrap_dec(y, g.ny), z)]
-                + phi[site_of(g, x, y, wrap_inc(z, g.nz))] + phi[site_of(g, x, y, wrap_dec(z, g.nz))]
-                - R(6) * p;
-    mu[s] = m.A * p + m.B * p * p * p - m.kappa * lap;
+    const R nb = phi[site_of(g, wrap_inc(x, g.nx), y, z)] + phi[site_of(g, wrap_dec(x, g.nx), y, z)]
+               + phi[site_of(g, x, wrap_inc(y, g.ny), z)] + phi[site_of(g, x, wrap_dec(y, g.ny), z)]
+               + phi[site_of(g, x, y, wrap_inc(z, g.nz))] + phi[site_of(g, x, y, wrap_dec(z, g.nz))];
+    mu[s] = chem_potential(phi[s], nb, m);
 }
 
 // Step, stage 3: force, velocity, collisions of f and g, and propagation
@@ -118,40 +116,41 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------
-// Initial state: f = feq(rho, u), g = geq(phi, u, mu(phi)), in double, then
-// encoded to the storage precision.
+// Initial state: f = feq(rho, u), g = geq(phi, u, mu(phi)), computed in the
+// arithmetic type of the precision from the FP64 inputs, then encoded.
 template <int P>
 __global__ void __launch_bounds__(kThreads)
-    k_init(Geom g, Model<double> m, double rho0, const double* __restrict__ phi,
+    k_init(Geom g, Model<typename Prec<P>::real_t> m, double rho0, const double* __restrict__ phi,
            const double* __restrict__ rho_in, const double* __restrict__ u_in, const float* __restrict__ ref,
            typename Prec<P>::store_t* __restrict__ fd, typename Prec<P>::store_t* __restrict__ gd) {
+    using R = typename Prec<P>::real_t;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.n) return;
     int x, y, z;
     site_coords(g, s, x, y, z);
-    const double p = phi[s];
-    const double lap = phi[site_of(g, wrap_inc(x, g.nx), y, z)] + phi[site_of(g, wrap_dec(x, g.nx), y, z)]
-                     + phi[site_of(g, x, wrap_inc(y, g.ny), z)] + phi[site_of(g, x, wrap_dec(y, g.ny), z)]
-                     + phi[site_of(g, x, y, wrap_inc(z, g.nz))] + phi[site_of(g, x, y, wrap_dec(z, g.nz))]
-                     - 6.0 * p;
-    const double mu = m.A * p + m.B * p * p * p - m.kappa * lap;
-    const double rho = rho_in ? rho_in[s] : rho0;
-    double ux = 0.0, uy = 0.0, uz = 0.0;
+    const R p = (R)phi[s];
+    const R lap = (R)phi[site_of(g, wrap_inc(x, g.nx), y, z)] + (R)phi[site_of(g, wrap_dec(x, g.nx), y, z)]
+                + (R)phi[site_of(g, x, wrap_inc(y, g.ny), z)] + (R)phi[site_of(g, x, wrap_dec(y, g.ny), z)]
+                + (R)phi[site_of(g, x, y, wrap_inc(z, g.nz))] + (R)phi[site_of(g, x, y, wrap_dec(z, g.nz))]
+                - R(6) * p;
+    const R mu = m.A * p + m.B * p * p * p - m.kappa * lap;
+    const R rho = (R)(rho_in ? rho_in[s] : rho0);
+    R ux = R(0), uy = R(0), uz = R(0);
     if (u_in) {
-        ux = u_in[s];
-        uy = u_in[g.n + s];
-        uz = u_in[2 * g.n + s];
+        ux = (R)u_in[s];
+        uy = (R)u_in[g.n + s];
+        uz = (R)u_in[2 * g.n + s];
     }
-    const double uu = ux * ux + uy * uy + uz * uz;
-    const double dev = m.Gamma * mu - p / 3.0;
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R dev = m.Gamma * mu - p / R(3);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-        const double feq = wgt<double>(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-        const double geq = wgt<double>(i) * (p + 3.0 * p * cu + 4.5 * dev * (c2(i) - 1) + 4.5 * p * cu * cu
-                                             - 1.5 * p * uu);
-        fd[i * g.npad + s] = Prec<P>::encode_d(feq, ref[i]);
-        gd[i * g.npad + s] = Prec<P>::encode_d(geq, ref[Q + i]);
+        const R cu = cdot(i, ux, uy, uz);
+        const R feq = wgt<R>(i) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+        const R geq = wgt<R>(i) * (p + R(3) * p * cu + R(4.5) * dev * R(c2(i) - 1) + R(4.5) * p * cu * cu
+                                   - R(1.5) * p * uu);
+        fd[i * g.npad + s] = Prec<P>::encode_d((double)feq, ref[i]);
+        gd[i * g.npad + s] = Prec<P>::encode_d((double)geq, ref[Q + i]);
     }
 }
 
@@ -211,18 +210,25 @@ __global__ void __launch_bounds__(kRedThreads)
     k_totals(Geom g, const typename Prec<P>::store_t* __restrict__ fs,
              const typename Prec<P>::store_t* __restrict__ gs, const float* __restrict__ ref,
              double* __restrict__ partials) {
+    // Each site's moments are summed in the arithmetic type of the precision
+    // (as the step itself forms them); sites accumulate in FP64.
+    using R = typename Prec<P>::real_t;
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.n; s += stride) {
+        R rho = R(0), phi = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double fi = Prec<P>::decode_d(fs[i * g.npad + s], ref[i]);
-            v[0] += fi;
-            v[2] += cx(i) * fi;
-            v[3] += cy(i) * fi;
-            v[4] += cz(i) * fi;
-            v[1] += Prec<P>::decode_d(gs[i * g.npad + s], ref[Q + i]);
+            const R fi = Prec<P>::decode(fs[i * g.npad + s], ref[i]);
+            rho += fi;
+            add_c(i, fi, jx, jy, jz);
+            phi += Prec<P>::decode(gs[i * g.npad + s], ref[Q + i]);
         }
+        v[0] += (double)rho;
+        v[1] += (double)phi;
+        v[2] += (double)jx;
+        v[3] += (double)jy;
+        v[4] += (double)jz;
     }
     block_sum_store<5>(v, partials + (long long)blockIdx.x * kRedFields);
 }
@@ -342,29 +348,38 @@ cudaError_t init_p(ld_ctx* c, const double* phi, const double* rho, const double
     } else {
         k_default_refs<<<1, 32, 0, c->stream>>>(c->prm.rho0, c->ref);
     }
-    k_init<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, m, c->prm.rho0, phi, rho, u, c->ref,
+    k_init<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, model_of<typename Prec<P>::real_t>(c->prm),
+                                                           c->prm.rho0, phi, rho, u, c->ref,
                                                            (S*)f_of(c, c->cur), (S*)g_of(c, c->cur));
     return cudaGetLastError();
 }
 
+// phi and mu of a state into `fields` ([phi npad][mu npad]), or into the
+// context's scratch when fields is null.
 template <int P>
-cudaError_t phi_mu_p(ld_ctx* c, const void* state) {
+cudaError_t phi_mu_p(ld_ctx* c, const void* state, void* fields = nullptr) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     const Geom g = to_dev(c->geom);
-    k_phi<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, (const S*)g_part(c, state), c->ref, (R*)c->phi);
-    k_mu<R><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, model_of<R>(c->prm), (const R*)c->phi, (R*)c->mu);
+    R* phi = fields ? (R*)fields : (R*)c->phi;
+    R* mu = fields ? (R*)fields + g.npad : (R*)c->mu;
+    k_phi<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, (const S*)g_part(c, state), c->ref, phi);
+    k_mu<R><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, model_of<R>(c->prm), phi, mu);
     return cudaGetLastError();
 }
 
 template <int P>
-cudaError_t collide_p(ld_ctx* c, const void* src, void* dst) {
+cudaError_t collide_p(ld_ctx* c, const void* src, void* dst, void* fields) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     const Geom g = to_dev(c->geom);
+    cudaError_t e = phi_mu_p<P>(c, src, fields);
+    if (e != cudaSuccess) return e;
+    const R* phi = fields ? (const R*)fields : (const R*)c->phi;
+    const R* mu = fields ? (const R*)fields + g.npad : (const R*)c->mu;
     k_collide<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(
         g, model_of<R>(c->prm), (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
-        (S*)g_part(c, dst), (const R*)c->phi, (const R*)c->mu, c->ref);
+        (S*)g_part(c, dst), phi, mu, c->ref);
     return cudaGetLastError();
 }
 

@@ -81,14 +81,14 @@ inline void* g_of(const ld_ctx* c, int buf) { return g_part(c, c->dist[buf]); }
     namespace NS {                                                                                \
     cudaError_t init(ld_ctx* c, const double* phi, const double* rho, const double* u);          \
     cudaError_t phi_mu(ld_ctx* c, const void* state);                                             \
-    cudaError_t collide_generic(ld_ctx* c, const void* src, void* dst);                           \
+    cudaError_t collide_generic(ld_ctx* c, const void* src, void* dst, void* fields);             \
     cudaError_t macros(ld_ctx* c, double* rho, double* u, double* phi, double* grad_phi);         \
     cudaError_t totals(ld_ctx* c, double* totals);                                                \
     cudaError_t decode(ld_ctx* c, double* f, double* g);                                          \
     cudaError_t encode(ld_ctx* c, const double* f, const double* g);                              \
-    cudaError_t step_fused_regs(ld_ctx* c, const void* src, void* dst);                           \
-    cudaError_t step_tma(ld_ctx* c, const void* src, void* dst);                                  \
-    cudaError_t adj_step(ld_ctx* c, const void* state_t, double* grad);                           \
+    cudaError_t step_fused_regs(ld_ctx* c, const void* src, void* dst, void* fields);             \
+    cudaError_t step_tma(ld_ctx* c, const void* src, void* dst, void* fields);                    \
+    cudaError_t adj_step(ld_ctx* c, const void* state_t, const void* fields_t, double* grad);     \
     cudaError_t adj_seed(ld_ctx* c, const double* phibar);                                        \
     cudaError_t adj_init(ld_ctx* c, const double* phi0, const double* u0, double* gphi0, double* grad); \
     cudaError_t adj_io(ld_ctx* c, int to_double, double* fbar, double* gbar);                     \
@@ -126,8 +126,8 @@ inline cudaError_t launch_decode(ld_ctx* c, double* f, double* g) {
 inline cudaError_t launch_encode(ld_ctx* c, const double* f, const double* g) {
     return is_f64(c) ? f64::encode(c, f, g) : lp::encode(c, f, g);
 }
-inline cudaError_t launch_adj_step(ld_ctx* c, const void* st, double* grad) {
-    return is_f64(c) ? f64::adj_step(c, st, grad) : lp::adj_step(c, st, grad);
+inline cudaError_t launch_adj_step(ld_ctx* c, const void* st, const void* fields, double* grad) {
+    return is_f64(c) ? f64::adj_step(c, st, fields, grad) : lp::adj_step(c, st, fields, grad);
 }
 inline cudaError_t launch_adj_seed(ld_ctx* c, const double* pb) {
     return is_f64(c) ? f64::adj_seed(c, pb) : lp::adj_seed(c, pb);
@@ -140,15 +140,15 @@ inline cudaError_t launch_adj_io(ld_ctx* c, int to_double, double* fbar, double*
 }
 
 // One full step from the state in `src` to the state in `dst` (distinct
-// buffers) with the context's step kernel.
-inline cudaError_t launch_step(ld_ctx* c, const void* src, void* dst) {
-    if (c->step_kernel == kStepGeneric) {
-        cudaError_t e = launch_phi_mu(c, src);
-        if (e != cudaSuccess) return e;
-        return is_f64(c) ? f64::collide_generic(c, src, dst) : lp::collide_generic(c, src, dst);
-    }
-    if (c->step_kernel == kStepTma) return is_f64(c) ? f64::step_tma(c, src, dst) : lp::step_tma(c, src, dst);
-    return is_f64(c) ? f64::step_fused_regs(c, src, dst) : lp::step_fused_regs(c, src, dst);
+// buffers) with the context's step kernel; when `fields` is not null the phi
+// and mu of the source state are also written there ([phi npad][mu npad],
+// arithmetic type).
+inline cudaError_t launch_step(ld_ctx* c, const void* src, void* dst, void* fields = nullptr) {
+    if (c->step_kernel == kStepGeneric)
+        return is_f64(c) ? f64::collide_generic(c, src, dst, fields) : lp::collide_generic(c, src, dst, fields);
+    if (c->step_kernel == kStepTma)
+        return is_f64(c) ? f64::step_tma(c, src, dst, fields) : lp::step_tma(c, src, dst, fields);
+    return is_f64(c) ? f64::step_fused_regs(c, src, dst, fields) : lp::step_fused_regs(c, src, dst, fields);
 }
 
 }  // namespace ld

@@ -65,7 +65,8 @@ template <int P>
 __global__ void __launch_bounds__(PipeLayout<P>::NT, 2)
     k_step_tma(Geom g, Model<typename Prec<P>::real_t> m, int zc, const typename Prec<P>::store_t* __restrict__ fs,
                const typename Prec<P>::store_t* __restrict__ gs, typename Prec<P>::store_t* __restrict__ fd,
-               typename Prec<P>::store_t* __restrict__ gd, const float* __restrict__ ref_g, int* __restrict__ status) {
+               typename Prec<P>::store_t* __restrict__ gd, const float* __restrict__ ref_g, int* __restrict__ status,
+               typename Prec<P>::real_t* __restrict__ phi_out, typename Prec<P>::real_t* __restrict__ mu_out) {
     using L = PipeLayout<P>;
     using S = typename L::S;
     using R = typename L::R;
@@ -173,9 +174,8 @@ __global__ void __launch_bounds__(PipeLayout<P>::NT, 2)
         for (int idx = tid; idx < MH * MW; idx += NT) {
             const int mx = idx % MW, my = idx / MW;
             const int c = (my + 1) * PW + mx + 1;
-            const R ph = mid[c];
-            const R lap = mid[c + 1] + mid[c - 1] + mid[c + PW] + mid[c - PW] + hi[c] + lo[c] - R(6) * ph;
-            dst[idx] = m.A * ph + m.B * ph * ph * ph - m.kappa * lap;
+            const R nb = mid[c + 1] + mid[c - 1] + mid[c + PW] + mid[c - PW] + hi[c] + lo[c];
+            dst[idx] = chem_potential(mid[c], nb, m);
         }
     };
 
@@ -229,6 +229,10 @@ __global__ void __launch_bounds__(PipeLayout<P>::NT, 2)
         const R gmz = R(0.5) * (mus[ms(k + 1) * (MH * MW) + (ty + 1) * MW + tx + 1] -
                                 mus[ms(k - 1) * (MH * MW) + (ty + 1) * MW + tx + 1]);
         const R Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
+        if (phi_out) {  // fields of the source state, for the adjoint
+            phi_out[s] = ph;
+            mu_out[s] = muc;
+        }
 
         const S* fb = F + (size_t)tslot(k) * L::FBOX + ty * TX + tx;
         R f[Q];
@@ -305,7 +309,7 @@ bool pipe_supported_p(int nx, int ny, int nz) {
 }
 
 template <int P>
-cudaError_t step_tma_p(ld_ctx* c, const void* src, void* dst) {
+cudaError_t step_tma_p(ld_ctx* c, const void* src, void* dst, void* fields) {
     using L = PipeLayout<P>;
     using S = typename L::S;
     using R = typename L::R;
@@ -320,8 +324,9 @@ cudaError_t step_tma_p(ld_ctx* c, const void* src, void* dst) {
     const dim3 grid(g.nx / L::TX, g.ny / L::TY, g.nz / zc);
     k_step_tma<P><<<grid, L::NT, L::BYTES, c->stream>>>(g, model_of<R>(c->prm), zc, (const S*)f_part(c, src),
                                                         (const S*)g_part(c, src), (S*)f_part(c, dst),
-                                                        (S*)g_part(c, dst), c->ref,
-                                                        c->status);
+                                                        (S*)g_part(c, dst), c->ref, c->status,
+                                                        fields ? (R*)fields : nullptr,
+                                                        fields ? (R*)fields + c->geom.npad : nullptr);
     return cudaGetLastError();
 }
 

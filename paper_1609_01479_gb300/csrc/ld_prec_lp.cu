@@ -20,17 +20,25 @@ cudaError_t init(ld_ctx* c, const double* phi, const double* rho, const double* 
     LD_LP_DISPATCH(init_p, c, phi, rho, u);
 }
 cudaError_t phi_mu(ld_ctx* c, const void* state) { LD_LP_DISPATCH(phi_mu_p, c, state); }
-cudaError_t collide_generic(ld_ctx* c, const void* src, void* dst) { LD_LP_DISPATCH(collide_p, c, src, dst); }
+cudaError_t collide_generic(ld_ctx* c, const void* src, void* dst, void* fields) {
+    LD_LP_DISPATCH(collide_p, c, src, dst, fields);
+}
 cudaError_t macros(ld_ctx* c, double* rho, double* u, double* phi, double* gphi) {
     LD_LP_DISPATCH(macros_p, c, rho, u, phi, gphi);
 }
 cudaError_t totals(ld_ctx* c, double* t) { LD_LP_DISPATCH(totals_p, c, t); }
 cudaError_t decode(ld_ctx* c, double* f, double* g) { LD_LP_DISPATCH(decode_p, c, f, g); }
 cudaError_t encode(ld_ctx* c, const double* f, const double* g) { LD_LP_DISPATCH(encode_p, c, f, g); }
-cudaError_t step_fused_regs(ld_ctx* c, const void* src, void* dst) { LD_LP_DISPATCH(step_fused_p, c, src, dst); }
-cudaError_t step_tma(ld_ctx* c, const void* src, void* dst) { LD_LP_DISPATCH(step_tma_p, c, src, dst); }
+cudaError_t step_fused_regs(ld_ctx* c, const void* src, void* dst, void* fields) {
+    LD_LP_DISPATCH(step_fused_p, c, src, dst, fields);
+}
+cudaError_t step_tma(ld_ctx* c, const void* src, void* dst, void* fields) {
+    LD_LP_DISPATCH(step_tma_p, c, src, dst, fields);
+}
 bool regs_supported(int nx, int ny, int nz) { return fused_supported_impl(nx, ny, nz); }
-cudaError_t adj_step(ld_ctx* c, const void* st, double* grad) { LD_LP_DISPATCH(adj_step_p, c, st, grad); }
+cudaError_t adj_step(ld_ctx* c, const void* st, const void* fields, double* grad) {
+    LD_LP_DISPATCH(adj_step_p, c, st, fields, grad);
+}
 cudaError_t adj_seed(ld_ctx* c, const double* pb) { LD_LP_DISPATCH(adj_seed_p, c, pb); }
 cudaError_t adj_init(ld_ctx* c, const double* phi0, const double* u0, double* gphi0, double* grad) {
     LD_LP_DISPATCH(adj_init_p, c, phi0, u0, gphi0, grad);

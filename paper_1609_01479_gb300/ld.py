@@ -64,11 +64,12 @@ _SIGNATURES = {
     "ld_state_bytes": (ctypes.c_size_t, [_VP]),
     "ld_save_state": (ctypes.c_int, [_VP, _VP]),
     "ld_load_state": (ctypes.c_int, [_VP, _VP]),
-    "ld_step_between": (ctypes.c_int, [_VP, _VP, _VP]),
+    "ld_fields_bytes": (ctypes.c_size_t, [_VP]),
+    "ld_step_between": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "ld_adjoint_workspace_bytes": (ctypes.c_size_t, [_VP]),
     "ld_adjoint_attach": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "ld_adjoint_seed": (ctypes.c_int, [_VP, _VP]),
-    "ld_adjoint_step": (ctypes.c_int, [_VP, _VP, _VP]),
+    "ld_adjoint_step": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "ld_adjoint_init": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "ld_adjoint_get": (ctypes.c_int, [_VP, _VP, _VP]),
     "ld_adjoint_set": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -191,8 +192,12 @@ def ld_load_state(ctx, buf):
     return _call("ld_load_state", ctx, _ptr(buf))
 
 
-def ld_step_between(ctx, src_state, dst_state):
-    return _call("ld_step_between", ctx, _ptr(src_state), _ptr(dst_state))
+def ld_fields_bytes(ctx) -> int:
+    return int(lib().ld_fields_bytes(ctx))
+
+
+def ld_step_between(ctx, src_state, dst_state, fields_out=None):
+    return _call("ld_step_between", ctx, _ptr(src_state), _ptr(dst_state), _ptr(fields_out))
 
 
 def ld_adjoint_workspace_bytes(ctx) -> int:
@@ -207,8 +212,8 @@ def ld_adjoint_seed(ctx, phibar):
     return _call("ld_adjoint_seed", ctx, _ptr(phibar))
 
 
-def ld_adjoint_step(ctx, state_t, grad_params=None):
-    return _call("ld_adjoint_step", ctx, _ptr(state_t), _ptr(grad_params))
+def ld_adjoint_step(ctx, state_t, grad_params=None, fields_t=None):
+    return _call("ld_adjoint_step", ctx, _ptr(state_t), _ptr(fields_t), _ptr(grad_params))
 
 
 def ld_adjoint_init(ctx, phi0, grad_phi0, u0=None, grad_params=None):
