@@ -183,33 +183,52 @@ __device__ __forceinline__ void guo_velocity(float rho, float jx, float jy, floa
 }
 
 // BGK + Guo collision of f in place.
+//
+// In FP32 the rest equilibrium is taken as rho minus the 18 moving ones (the
+// same value in exact arithmetic): the nearest floats to 1/3, 1/18 and 1/36
+// sum to 1 + 1.5e-8, and the formula for every direction would add that much
+// mass to each site at every step. FP64 evaluates the formula for all 19.
 template <class R>
 __device__ __forceinline__ void collide_f(R (&f)[Q], R rho, R ux, R uy, R uz, R Fx, R Fy, R Fz,
                                           const Model<R>& m) {
+    constexpr bool kRestByDifference = sizeof(R) == 4;
     const R uu = ux * ux + uy * uy + uz * uz;
     const R uF = ux * Fx + uy * Fy + uz * Fz;
+    R moving = R(0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 1; i < Q; ++i) {
         const R cu = cdot(i, ux, uy, uz);
         const R cF = cdot(i, Fx, Fy, Fz);
         const R feq = wgt<R>(i) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
         const R src = m.force_pre * wgt<R>(i) * (R(3) * (cF - uF) + R(9) * cu * cF);
         f[i] = f[i] - m.omega_f * (f[i] - feq) + src;
+        if (kRestByDifference) moving += feq;
     }
+    // c_0 = 0: feq_0 = w_0 rho (1 - 3/2 u.u), src_0 = pre w_0 (-3 u.F)
+    const R feq0 = kRestByDifference ? rho - moving : wgt<R>(0) * rho * (R(1) - R(1.5) * uu);
+    const R src0 = m.force_pre * wgt<R>(0) * (R(3) * (-uF));
+    f[0] = f[0] - m.omega_f * (f[0] - feq0) + src0;
 }
 
-// BGK collision of g in place.
+// BGK collision of g in place (FP32: rest equilibrium by difference from
+// phi, for the same reason as in collide_f).
 template <class R>
 __device__ __forceinline__ void collide_g(R (&g)[Q], R phi, R mu, R ux, R uy, R uz, const Model<R>& m) {
+    constexpr bool kRestByDifference = sizeof(R) == 4;
     const R uu = ux * ux + uy * uy + uz * uz;
     const R dev = m.Gamma * mu - phi / R(3);
+    R moving = R(0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 1; i < Q; ++i) {
         const R cu = cdot(i, ux, uy, uz);
         const R geq = wgt<R>(i) * (phi + R(3) * phi * cu + R(4.5) * dev * R(c2(i) - 1)
                                    + R(4.5) * phi * cu * cu - R(1.5) * phi * uu);
         g[i] = g[i] - m.omega_g * (g[i] - geq);
+        if (kRestByDifference) moving += geq;
     }
+    // c_0 = 0, |c_0|^2 - 1 = -1: geq_0 = w_0 (phi - 9/2 dev - 3/2 phi u.u)
+    const R geq0 = kRestByDifference ? phi - moving : wgt<R>(0) * ((phi - R(4.5) * dev) - R(1.5) * phi * uu);
+    g[0] = g[0] - m.omega_g * (g[0] - geq0);
 }
 
 }  // namespace ld

@@ -97,26 +97,43 @@ def _droplet(ld, prec, n, R, steps):
 
 
 @pytest.mark.slow
-def test_droplet_laplace_law_and_precisions(ld):
-    """Droplets of radius 16 and 24 in a 128^3 box relaxed for 2000 steps.
-    The pressure jump p_b(phi_in) - p_b(phi_out), p_b = A phi^2/2 + 3B phi^4/4,
-    scales as 1/R_eff (Laplace): dp R_eff / 2 agrees between the radii within
-    5 %, and that tension lies within 30 % of the continuum
-    sigma = sqrt(-8 kappa A^3 / (9 B^2)) (the discrete interface, xi = 1.13
-    sites, is narrower than the continuum one). The FP16/BF16 deviation forms
-    stay close to FP32 and conserve mass to their storage rounding."""
-    n, steps = 128, 2000
+def test_droplet_laplace_law(ld):
+    """Droplets of radius 12 and 16 in a 64^3 box, relaxed for 20000 steps:
+    about six relaxation times of the slowest bulk mode of phi,
+    L^2 / (4 pi^2 D) with D = Gamma (tau_g - 1/2)(A + 3B) ~ 0.031. The pressure
+    jump p_b(phi_in) - p_b(phi_out), p_b = A phi^2/2 + 3B phi^4/4, follows the
+    Laplace law dp = 2 sigma / R_eff up to a curvature correction that falls
+    with R: the tension dp R_eff / 2 moves towards the continuum
+    sigma = sqrt(-8 kappa A^3 / (9 B^2)) as R grows and is within 10 % of it at
+    R = 16."""
+    n, steps = 64, 20000
     A, B, kappa = -0.0625, 0.0625, 0.04
     sigma = math.sqrt(-8 * kappa * A ** 3 / (9 * B * B))
+    d12 = _droplet(ld, "fp32", n, 12.0, steps)
     d16 = _droplet(ld, "fp32", n, 16.0, steps)
-    d24 = _droplet(ld, "fp32", n, 24.0, steps)
+    s12 = d12["dp"] * d12["reff"] / 2
     s16 = d16["dp"] * d16["reff"] / 2
-    s24 = d24["dp"] * d24["reff"] / 2
-    assert abs(s16 / s24 - 1.0) < 0.05, (s16, s24)
-    assert abs(s24 / sigma - 1.0) < 0.30, (s24, sigma)
-    assert d24["mass_drift"] < 1e-6
-    for prec, tol in (("fp16dev", 5e-3), ("bf16dev", 5e-2)):
-        d = _droplet(ld, prec, n, 24.0, steps)
-        e = np.linalg.norm(d["phi"] - d24["phi"]) / np.linalg.norm(d24["phi"])
+    assert abs(s16 - sigma) < abs(s12 - sigma), (s12, s16, sigma)
+    assert abs(s16 / sigma - 1.0) < 0.10, (s12, s16, sigma)
+    # FP32 storage: a step can move total mass by at most the rounding of the
+    # 19 stored values per site, 19 * 2^-25 relative; the drift measured over
+    # the run must stay 100 times below that worst case.
+    assert d16["mass_drift"] < steps * 19 * 2.0 ** -25 / 100
+
+
+@pytest.mark.slow
+def test_droplet_precisions(ld):
+    """A droplet of radius 24 in a 128^3 box, 2000 steps: the FP16/BF16
+    deviation forms stay close to FP32 and keep the droplet's size. Each step
+    rounds the stored deviations to 2^-p of their size (p = 11 for FP16, 8 for
+    BF16), and in the droplet the g deviations are as large as phi itself, so
+    phi may wander from FP32 by about 2^-p sqrt(steps) in relative L2."""
+    n, steps, R = 128, 2000, 24.0
+    ref = _droplet(ld, "fp32", n, R, steps)
+    assert ref["mass_drift"] < steps * 19 * 2.0 ** -25 / 100
+    for prec, p in (("fp16dev", 11), ("bf16dev", 8)):
+        tol = 2.0 ** -p * math.sqrt(steps)
+        d = _droplet(ld, prec, n, R, steps)
+        e = np.linalg.norm(d["phi"] - ref["phi"]) / np.linalg.norm(ref["phi"])
         assert e < tol, (prec, e)
-        assert abs(d["reff"] - d24["reff"]) < 0.5
+        assert abs(d["reff"] - ref["reff"]) < 0.5
