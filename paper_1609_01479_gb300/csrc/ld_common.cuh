@@ -184,17 +184,22 @@ __device__ __forceinline__ void guo_velocity(float rho, float jx, float jy, floa
 
 // BGK + Guo collision of f in place.
 //
-// In FP32 the rest equilibrium is taken as rho minus the 18 moving ones (the
-// same value in exact arithmetic): the nearest floats to 1/3, 1/18 and 1/36
-// sum to 1 + 1.5e-8, and the formula for every direction would add that much
-// mass to each site at every step. FP64 evaluates the formula for all 19.
+// FP64 evaluates the equilibrium and the source term direction by direction,
+// in the same operation order as the formulas above.
+//
+// FP32 (also the arithmetic of the 16-bit forms) works on opposite pairs
+// (i, i+1), c_{i+1} = -c_i: c.u and c.F change sign within a pair, so
+//   feq_(i,i+1) = w rho (1 - 3/2 u.u + 9/2 (c.u)^2) +- 3 w rho c.u
+//   src_(i,i+1) = pre w (9 (c.u)(c.F) - 3 u.F)        +- 3 pre w c.F
+// and each pair shares its symmetric part. The rest equilibrium is rho minus
+// the 18 moving ones (the same value in exact arithmetic): the nearest
+// floats to 1/3, 1/18, 1/36 sum to 1 + 1.5e-8, and the formula for every
+// direction would add that much mass to each site at every step.
 template <class R>
 __device__ __forceinline__ void collide_f(R (&f)[Q], R rho, R ux, R uy, R uz, R Fx, R Fy, R Fz,
                                           const Model<R>& m) {
-    constexpr bool kRestByDifference = sizeof(R) == 4;
     const R uu = ux * ux + uy * uy + uz * uz;
     const R uF = ux * Fx + uy * Fy + uz * Fz;
-    R moving = R(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const R cu = cdot(i, ux, uy, uz);
@@ -202,33 +207,81 @@ __device__ __forceinline__ void collide_f(R (&f)[Q], R rho, R ux, R uy, R uz, R 
         const R feq = wgt<R>(i) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
         const R src = m.force_pre * wgt<R>(i) * (R(3) * (cF - uF) + R(9) * cu * cF);
         f[i] = f[i] - m.omega_f * (f[i] - feq) + src;
-        if (kRestByDifference) moving += feq;
     }
     // c_0 = 0: feq_0 = w_0 rho (1 - 3/2 u.u), src_0 = pre w_0 (-3 u.F)
-    const R feq0 = kRestByDifference ? rho - moving : wgt<R>(0) * rho * (R(1) - R(1.5) * uu);
+    const R feq0 = wgt<R>(0) * rho * (R(1) - R(1.5) * uu);
     const R src0 = m.force_pre * wgt<R>(0) * (R(3) * (-uF));
     f[0] = f[0] - m.omega_f * (f[0] - feq0) + src0;
 }
 
-// BGK collision of g in place (FP32: rest equilibrium by difference from
-// phi, for the same reason as in collide_f).
+template <>
+__device__ __forceinline__ void collide_f<float>(float (&f)[Q], float rho, float ux, float uy, float uz, float Fx,
+                                                 float Fy, float Fz, const Model<float>& m) {
+    const float uu = ux * ux + uy * uy + uz * uz;
+    const float uF = ux * Fx + uy * Fy + uz * Fz;
+    const float base = 1.0f - 1.5f * uu;
+    const float keep = 1.0f - m.omega_f;
+    float moving = 0.0f;  // sum of the symmetric equilibrium parts (each counted once)
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float w = wgt<float>(i);
+        const float wr = w * rho, pw = m.force_pre * w;
+        const float cu = cdot(i, ux, uy, uz);
+        const float cF = cdot(i, Fx, Fy, Fz);
+        const float feq_sym = wr * (base + 4.5f * cu * cu);
+        const float feq_anti = 3.0f * wr * cu;
+        const float src_sym = pw * (9.0f * cu * cF - 3.0f * uF);
+        const float src_anti = 3.0f * pw * cF;
+        const float sym = m.omega_f * feq_sym + src_sym;
+        const float anti = m.omega_f * feq_anti + src_anti;
+        f[i] = keep * f[i] + (sym + anti);
+        f[i + 1] = keep * f[i + 1] + (sym - anti);
+        moving += feq_sym;
+    }
+    const float feq0 = rho - 2.0f * moving;
+    const float src0 = m.force_pre * wgt<float>(0) * (-3.0f * uF);
+    f[0] = keep * f[0] + (m.omega_f * feq0 + src0);
+}
+
+// BGK collision of g in place; FP64 direction by direction, FP32 on opposite
+// pairs with the rest equilibrium phi minus the moving ones (as in collide_f).
 template <class R>
 __device__ __forceinline__ void collide_g(R (&g)[Q], R phi, R mu, R ux, R uy, R uz, const Model<R>& m) {
-    constexpr bool kRestByDifference = sizeof(R) == 4;
     const R uu = ux * ux + uy * uy + uz * uz;
     const R dev = m.Gamma * mu - phi / R(3);
-    R moving = R(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const R cu = cdot(i, ux, uy, uz);
         const R geq = wgt<R>(i) * (phi + R(3) * phi * cu + R(4.5) * dev * R(c2(i) - 1)
                                    + R(4.5) * phi * cu * cu - R(1.5) * phi * uu);
         g[i] = g[i] - m.omega_g * (g[i] - geq);
-        if (kRestByDifference) moving += geq;
     }
     // c_0 = 0, |c_0|^2 - 1 = -1: geq_0 = w_0 (phi - 9/2 dev - 3/2 phi u.u)
-    const R geq0 = kRestByDifference ? phi - moving : wgt<R>(0) * ((phi - R(4.5) * dev) - R(1.5) * phi * uu);
+    const R geq0 = wgt<R>(0) * ((phi - R(4.5) * dev) - R(1.5) * phi * uu);
     g[0] = g[0] - m.omega_g * (g[0] - geq0);
+}
+
+template <>
+__device__ __forceinline__ void collide_g<float>(float (&g)[Q], float phi, float mu, float ux, float uy, float uz,
+                                                 const Model<float>& m) {
+    const float uu = ux * ux + uy * uy + uz * uz;
+    const float dev = m.Gamma * mu - phi / 3.0f;
+    const float pbase = phi * (1.0f - 1.5f * uu);
+    const float keep = 1.0f - m.omega_g;
+    float moving = 0.0f;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float w = wgt<float>(i);
+        const float cu = cdot(i, ux, uy, uz);
+        const float geq_sym = w * (pbase + 4.5f * dev * float(c2(i) - 1) + 4.5f * phi * cu * cu);
+        const float geq_anti = 3.0f * w * phi * cu;
+        const float sym = m.omega_g * geq_sym, anti = m.omega_g * geq_anti;
+        g[i] = keep * g[i] + (sym + anti);
+        g[i + 1] = keep * g[i + 1] + (sym - anti);
+        moving += geq_sym;
+    }
+    const float geq0 = phi - 2.0f * moving;
+    g[0] = keep * g[0] + m.omega_g * geq0;
 }
 
 }  // namespace ld

@@ -24,11 +24,18 @@ namespace {
 
 constexpr int kTX = 32;
 
+// Resident CTAs per SM the kernel is compiled for: three 256-thread CTAs
+// (80 registers a thread) with FP32 arithmetic, two with FP64.
+template <int P>
+constexpr int fused_ctas_per_sm() {
+    return sizeof(typename Prec<P>::real_t) == 4 ? 3 : 2;
+}
+
 // Periodic image of a coordinate at most one period outside [0, n).
 __device__ __forceinline__ int wrap_once(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 template <int P, int TY>
-__global__ void __launch_bounds__(kTX * TY, 2)
+__global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     k_step_fused(Geom g, Model<typename Prec<P>::real_t> m, int zc,
                  const typename Prec<P>::store_t* __restrict__ fs, const typename Prec<P>::store_t* __restrict__ gs,
                  typename Prec<P>::store_t* __restrict__ fd, typename Prec<P>::store_t* __restrict__ gd,
@@ -147,15 +154,23 @@ __global__ void __launch_bounds__(kTX * TY, 2)
 
 constexpr int kTY = 8;
 
-// Planes per CTA: the largest of 32, 16, 8, 4 dividing nz that still gives
-// at least ~8 CTAs per SM of work (152 SMs), else the smallest divisor.
-int choose_zc(int nx, int ny, int nz) {
+// Planes per CTA. `per_sm` CTAs are resident per SM, and each CTA pays a
+// prologue worth about two collided planes (four extra phi planes and the
+// pipeline start); pick the divisor of nz among 64..4 that minimises
+// waves x (planes per CTA + 2).
+int choose_zc(int nx, int ny, int nz, int num_sms = 152, int per_sm = 2) {
     const long long cols = (long long)(nx / kTX) * (ny / kTY);
+    const long long slots = (long long)per_sm * num_sms;
     int best = 0;
-    for (int zc = 32; zc >= 4; zc /= 2) {
+    long long best_cost = 0;
+    for (int zc = 64; zc >= 4; zc /= 2) {
         if (nz % zc) continue;
-        best = zc;
-        if (cols * (nz / zc) >= 8LL * 152) break;
+        const long long waves = (cols * (nz / zc) + slots - 1) / slots;
+        const long long cost = waves * (zc + 2);
+        if (best == 0 || cost < best_cost) {
+            best = zc;
+            best_cost = cost;
+        }
     }
     return best;
 }
@@ -165,7 +180,7 @@ cudaError_t step_fused_p(ld_ctx* c, const void* src, void* dst, void* fields) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
-    const int zc = choose_zc(g.nx, g.ny, g.nz);
+    const int zc = choose_zc(g.nx, g.ny, g.nz, c->num_sms, fused_ctas_per_sm<P>());
     const dim3 grid(g.nx / kTX, g.ny / kTY, g.nz / zc);
     k_step_fused<P, kTY><<<grid, kTX * kTY, 0, c->stream>>>(g, model_of<R>(c->prm), zc, (const S*)f_part(c, src),
                                                             (const S*)g_part(c, src), (S*)f_part(c, dst),
