@@ -19,6 +19,10 @@
 //   3. mubar(y) += sum_a (gmbar_a(y-e_a) - gmbar_a(y+e_a))/2   (transposed gradient);
 //   4. phibar(y) += (A + 3B phi^2) mubar - kappa lap(mubar)    (lap is symmetric);
 //      gbar_i(y,t) = (1-w_g) g*bar_i(y) + phibar(y).
+// The adjoint g is kept factored as gbar_i = G_i + P with a per-site scalar
+// P: step 2 writes G_i = (1-w_g) g*bar_i at the site it already owns, step 4
+// writes only P = phibar, and the next step's pull adds P of the source
+// site. This saves a full read and write pass over the 19 gbar values.
 // Parameter sums (FP64, fixed order): kappabar += sum mubar (-lap phi);
 // taubar_f = -(1/tau_f^2) sum_i,x f*bar_i (feq_i - f_i - S_i/2).
 #pragma once
@@ -45,13 +49,21 @@ __device__ __forceinline__ void block_sum_one(double v, double* out) {
     }
 }
 
+// Two resident 256-thread CTAs per SM for the local adjoint kernel: at three
+// (80 registers) it spills and runs 16% slower.
+template <int P>
+constexpr int adj_ctas_per_sm() {
+    return 2;
+}
+
 // Step 1 + 2: local adjoint at every site.
 template <int P>
-__global__ void __launch_bounds__(kAdjThreads)
+__global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<P>())
     k_adj_local(Geom g, Model<typename Prec<P>::real_t> m, const typename Prec<P>::store_t* __restrict__ tf,
                 const typename Prec<P>::real_t* __restrict__ phi, const typename Prec<P>::real_t* __restrict__ mu,
                 const float* __restrict__ ref, const typename Prec<P>::real_t* __restrict__ fb1,
-                const typename Prec<P>::real_t* __restrict__ gb1, typename Prec<P>::real_t* __restrict__ fb0,
+                const typename Prec<P>::real_t* __restrict__ gb1, const typename Prec<P>::real_t* __restrict__ pb1,
+                typename Prec<P>::real_t* __restrict__ fb0, typename Prec<P>::real_t* __restrict__ gb0,
                 typename Prec<P>::real_t* __restrict__ gmb, typename Prec<P>::real_t* __restrict__ mub,
                 typename Prec<P>::real_t* __restrict__ phib, double* __restrict__ part) {
     using R = typename Prec<P>::real_t;
@@ -97,7 +109,8 @@ __global__ void __launch_bounds__(kAdjThreads)
             const long long o = site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny),
                                         step_coord(z, cz(i), g.nz));
             fbs[i] = fb1[i * g.npad + o];
-            const R gbs = gb1[i * g.npad + o];
+            const R gbs = gb1[i * g.npad + o] + pb1[o];
+            gb0[i * g.npad + s] = (R(1) - m.omega_g) * gbs;
             const R w = wgt<R>(i);
             const R cu = cdot(i, ux, uy, uz);
             const R cF = cdot(i, Fx, Fy, Fz);
@@ -170,11 +183,11 @@ __global__ void __launch_bounds__(kAdjThreads)
     block_sum_one(kappa_bar, part + 2 * (long long)blockIdx.x + 1);
 }
 
-// Step 4: phibar and gbar at t (pull of g*bar again).
+// Step 4: phibar, the per-site part P of gbar at t.
 template <class R>
 __global__ void __launch_bounds__(kAdjThreads)
-    k_adj_g(Geom g, Model<R> m, const R* __restrict__ phi, const R* __restrict__ mub, const R* __restrict__ phib,
-            const R* __restrict__ gb1, R* __restrict__ gb0) {
+    k_adj_p(Geom g, Model<R> m, const R* __restrict__ phi, const R* __restrict__ mub, const R* __restrict__ phib,
+            R* __restrict__ pb0) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.n) return;
     int x, y, z;
@@ -183,13 +196,7 @@ __global__ void __launch_bounds__(kAdjThreads)
     const R lapm = mub[site_of(g, wrap_inc(x, g.nx), y, z)] + mub[site_of(g, wrap_dec(x, g.nx), y, z)] +
                    mub[site_of(g, x, wrap_inc(y, g.ny), z)] + mub[site_of(g, x, wrap_dec(y, g.ny), z)] +
                    mub[site_of(g, x, y, wrap_inc(z, g.nz))] + mub[site_of(g, x, y, wrap_dec(z, g.nz))] - R(6) * mub[s];
-    const R pb = phib[s] + (m.A + R(3) * m.B * ph * ph) * mub[s] - m.kappa * lapm;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const long long o = site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny),
-                                    step_coord(z, cz(i), g.nz));
-        gb0[i * g.npad + s] = (R(1) - m.omega_g) * gb1[i * g.npad + o] + pb;
-    }
+    pb0[s] = phib[s] + (m.A + R(3) * m.B * ph * ph) * mub[s] - m.kappa * lapm;
 }
 
 // grad[0] += sum_b part[2b+1] (kappa); grad[1] += taub_scale * sum_b part[2b]
@@ -223,39 +230,43 @@ __global__ void __launch_bounds__(kAdjThreads)
     }
 }
 
-// Seed: fbar = 0, gbar_i = phibar (the adjoint of phi_T = sum_i g_i).
+// Seed: fbar = 0, gbar_i = phibar (the adjoint of phi_T = sum_i g_i), i.e.
+// G = 0 and P = phibar.
 template <class R>
 __global__ void __launch_bounds__(kAdjThreads)
-    k_adj_seed(Geom g, const double* __restrict__ phibar, R* __restrict__ fb, R* __restrict__ gb) {
+    k_adj_seed(Geom g, const double* __restrict__ phibar, R* __restrict__ fb, R* __restrict__ gb, R* __restrict__ pb) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.n) return;
-    const R v = (R)phibar[s];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         fb[i * g.npad + s] = R(0);
-        gb[i * g.npad + s] = v;
+        gb[i * g.npad + s] = R(0);
     }
+    pb[s] = (R)phibar[s];
 }
 
-// Initialiser adjoint, part 1: mubar(x) = sum_i gbar_i d geq_i / d mu.
+// Initialiser adjoint, part 1: mubar(x) = sum_i gbar_i d geq_i / d mu, in
+// the arithmetic type.
 template <class R>
 __global__ void __launch_bounds__(kAdjThreads)
-    k_adj_init_mu(Geom g, double Gamma, const R* __restrict__ gb, R* __restrict__ mub) {
+    k_adj_init_mu(Geom g, R Gamma, const R* __restrict__ gb, const R* __restrict__ pb, R* __restrict__ mub) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.n) return;
-    double acc = 0.0;
+    R acc = R(0);
+    const R p = pb[s];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) acc += (double)gb[i * g.npad + s] * wgt<double>(i) * 4.5 * Gamma * (c2(i) - 1);
-    mub[s] = (R)acc;
+    for (int i = 0; i < Q; ++i) acc += (gb[i * g.npad + s] + p) * (wgt<R>(i) * R(4.5) * R(c2(i) - 1));
+    mub[s] = Gamma * acc;
 }
 
 // Initialiser adjoint, part 2: dL/dphi0 and the kappa partials
 // (g = geq(phi0, u0, mu(phi0)); f does not depend on phi0, kappa or tau_f).
+// Per-site sums in the arithmetic type; outputs and partials in FP64.
 template <class R>
 __global__ void __launch_bounds__(kAdjThreads)
-    k_adj_init_phi(Geom g, Model<double> m, const double* __restrict__ phi0, const double* __restrict__ u0,
-                   const R* __restrict__ gb, const R* __restrict__ mub, double* __restrict__ grad_phi0,
-                   double* __restrict__ part) {
+    k_adj_init_phi(Geom g, Model<R> m, const double* __restrict__ phi0, const double* __restrict__ u0,
+                   const R* __restrict__ gb, const R* __restrict__ pb, const R* __restrict__ mub,
+                   double* __restrict__ grad_phi0, double* __restrict__ part) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double kappa_bar = 0.0;
     if (s < g.n) {
@@ -264,50 +275,55 @@ __global__ void __launch_bounds__(kAdjThreads)
         const long long sxp = site_of(g, wrap_inc(x, g.nx), y, z), sxm = site_of(g, wrap_dec(x, g.nx), y, z);
         const long long syp = site_of(g, x, wrap_inc(y, g.ny), z), sym = site_of(g, x, wrap_dec(y, g.ny), z);
         const long long szp = site_of(g, x, y, wrap_inc(z, g.nz)), szm = site_of(g, x, y, wrap_dec(z, g.nz));
-        double ux = 0.0, uy = 0.0, uz = 0.0;
+        R ux = R(0), uy = R(0), uz = R(0);
         if (u0) {
-            ux = u0[s];
-            uy = u0[g.n + s];
-            uz = u0[2 * g.n + s];
+            ux = (R)u0[s];
+            uy = (R)u0[g.n + s];
+            uz = (R)u0[2 * g.n + s];
         }
-        const double uu = ux * ux + uy * uy + uz * uz;
-        double acc = 0.0;
+        const R uu = ux * ux + uy * uy + uz * uz;
+        const R p = pb[s];
+        R acc = R(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-            acc += (double)gb[i * g.npad + s] * wgt<double>(i) *
-                   (1.0 + 3.0 * cu - 1.5 * (c2(i) - 1) + 4.5 * cu * cu - 1.5 * uu);
+            const R cu = cdot(i, ux, uy, uz);
+            acc += (gb[i * g.npad + s] + p) * wgt<R>(i) *
+                   (R(1) + R(3) * cu - R(1.5) * R(c2(i) - 1) + R(4.5) * cu * cu - R(1.5) * uu);
         }
-        const double ph = phi0[s];
-        const double mb = mub[s];
-        const double lapm = (double)mub[sxp] + mub[sxm] + mub[syp] + mub[sym] + mub[szp] + mub[szm] - 6.0 * mb;
-        grad_phi0[s] = acc + (m.A + 3.0 * m.B * ph * ph) * mb - m.kappa * lapm;
-        const double lap = phi0[sxp] + phi0[sxm] + phi0[syp] + phi0[sym] + phi0[szp] + phi0[szm] - 6.0 * ph;
-        kappa_bar = -mb * lap;
+        const R ph = (R)phi0[s];
+        const R mb = mub[s];
+        const R lapm = mub[sxp] + mub[sxm] + mub[syp] + mub[sym] + mub[szp] + mub[szm] - R(6) * mb;
+        grad_phi0[s] = (double)(acc + (m.A + R(3) * m.B * ph * ph) * mb - m.kappa * lapm);
+        const double lap = phi0[sxp] + phi0[sxm] + phi0[syp] + phi0[sym] + phi0[szp] + phi0[szm] - 6.0 * phi0[s];
+        kappa_bar = -(double)mb * lap;
     }
     if (threadIdx.x == 0) part[2 * (long long)blockIdx.x] = 0.0;  // no tau_f term in the initialiser
     block_sum_one(kappa_bar, part + 2 * (long long)blockIdx.x + 1);
 }
 
+// Adjoint state I/O as double[19][n]. For the g part `pb` is the per-site
+// term: read adds it; write stores the values in G and clears it.
 template <class R>
 __global__ void __launch_bounds__(kAdjThreads)
-    k_adj_io(Geom g, int to_double, R* __restrict__ a, double* __restrict__ d) {
+    k_adj_io(Geom g, int to_double, R* __restrict__ a, R* __restrict__ pb, double* __restrict__ d) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.n) return;
+    const R add = (pb && to_double) ? pb[s] : R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (to_double)
-            d[i * g.n + s] = (double)a[i * g.npad + s];
+            d[i * g.n + s] = (double)(a[i * g.npad + s] + add);
         else
             a[i * g.npad + s] = (R)d[i * g.n + s];
     }
+    if (pb && !to_double) pb[s] = R(0);
 }
 
 // ---------------------------------------------------------------------------
 template <int P>
 struct AdjPtrs {
     using R = typename Prec<P>::real_t;
-    R *fb1, *gb1, *fb0, *gb0, *gmb, *mub, *phib;
+    R *fb1, *gb1, *pb1, *fb0, *gb0, *pb0, *gmb, *mub, *phib;
 };
 
 template <int P>
@@ -319,8 +335,10 @@ AdjPtrs<P> adj_ptrs(ld_ctx* c, int in_buf) {
     R* b = (R*)c->adj[1 - in_buf];
     p.fb1 = a;
     p.gb1 = a + comp;
+    p.pb1 = (R*)c->adj_p[in_buf];
     p.fb0 = b;
     p.gb0 = b + comp;
+    p.pb0 = (R*)c->adj_p[1 - in_buf];
     p.gmb = (R*)c->adj_gmb;
     p.mub = (R*)c->adj_mub;
     p.phib = (R*)c->adj_phib;
@@ -342,9 +360,9 @@ cudaError_t adj_step_p(ld_ctx* c, const void* state_t, const void* fields_t, dou
     const Model<R> m = model_of<R>(c->prm);
     const unsigned nb = blocks_for(g.n);
     k_adj_local<P><<<nb, kAdjThreads, 0, c->stream>>>(g, m, (const S*)f_part(c, state_t), phi, mu, c->ref, p.fb1,
-                                                      p.gb1, p.fb0, p.gmb, p.mub, p.phib, c->adj_part);
+                                                      p.gb1, p.pb1, p.fb0, p.gb0, p.gmb, p.mub, p.phib, c->adj_part);
     k_adj_mu<R><<<nb, kAdjThreads, 0, c->stream>>>(g, phi, p.gmb, p.mub, c->adj_part);
-    k_adj_g<R><<<nb, kAdjThreads, 0, c->stream>>>(g, m, phi, p.mub, p.phib, p.gb1, p.gb0);
+    k_adj_p<R><<<nb, kAdjThreads, 0, c->stream>>>(g, m, phi, p.mub, p.phib, p.pb0);
     if (grad)
         k_adj_finalize<<<1, kAdjThreads, 0, c->stream>>>(c->adj_part, nb, -1.0 / (c->prm.tau_f * c->prm.tau_f),
                                                          grad);
@@ -356,7 +374,7 @@ cudaError_t adj_seed_p(ld_ctx* c, const double* phibar) {
     using R = typename Prec<P>::real_t;
     const Geom g = to_dev(c->geom);
     const AdjPtrs<P> p = adj_ptrs<P>(c, c->adj_cur);
-    k_adj_seed<R><<<blocks_for(g.n), kAdjThreads, 0, c->stream>>>(g, phibar, p.fb1, p.gb1);
+    k_adj_seed<R><<<blocks_for(g.n), kAdjThreads, 0, c->stream>>>(g, phibar, p.fb1, p.gb1, p.pb1);
     return cudaGetLastError();
 }
 
@@ -366,8 +384,8 @@ cudaError_t adj_init_p(ld_ctx* c, const double* phi0, const double* u0, double* 
     const Geom g = to_dev(c->geom);
     const AdjPtrs<P> p = adj_ptrs<P>(c, c->adj_cur);
     const unsigned nb = blocks_for(g.n);
-    k_adj_init_mu<R><<<nb, kAdjThreads, 0, c->stream>>>(g, c->prm.Gamma, p.gb1, p.mub);
-    k_adj_init_phi<R><<<nb, kAdjThreads, 0, c->stream>>>(g, model_of<double>(c->prm), phi0, u0, p.gb1, p.mub,
+    k_adj_init_mu<R><<<nb, kAdjThreads, 0, c->stream>>>(g, (R)c->prm.Gamma, p.gb1, p.pb1, p.mub);
+    k_adj_init_phi<R><<<nb, kAdjThreads, 0, c->stream>>>(g, model_of<R>(c->prm), phi0, u0, p.gb1, p.pb1, p.mub,
                                                          grad_phi0, c->adj_part);
     if (grad) k_adj_finalize<<<1, kAdjThreads, 0, c->stream>>>(c->adj_part, nb, 0.0, grad);
     return cudaGetLastError();
@@ -378,8 +396,8 @@ cudaError_t adj_io_p(ld_ctx* c, int to_double, double* fbar, double* gbar) {
     using R = typename Prec<P>::real_t;
     const Geom g = to_dev(c->geom);
     const AdjPtrs<P> p = adj_ptrs<P>(c, c->adj_cur);
-    if (fbar) k_adj_io<R><<<blocks_for(g.n), kAdjThreads, 0, c->stream>>>(g, to_double, p.fb1, fbar);
-    if (gbar) k_adj_io<R><<<blocks_for(g.n), kAdjThreads, 0, c->stream>>>(g, to_double, p.gb1, gbar);
+    if (fbar) k_adj_io<R><<<blocks_for(g.n), kAdjThreads, 0, c->stream>>>(g, to_double, p.fb1, nullptr, fbar);
+    if (gbar) k_adj_io<R><<<blocks_for(g.n), kAdjThreads, 0, c->stream>>>(g, to_double, p.gb1, p.pb1, gbar);
     return cudaGetLastError();
 }
 

@@ -333,7 +333,7 @@ int ld_load_state(ld_ctx* c, const void* dev_buf) {
 
 namespace {
 struct AdjLayout {
-    size_t adj, gmb, mub, phib, part, total;
+    size_t adj, gmb, mub, phib, pfield, part, total;
 };
 AdjLayout adj_layout_of(const ld_ctx* c) {
     const size_t npad = (size_t)c->geom.npad;
@@ -349,6 +349,8 @@ AdjLayout adj_layout_of(const ld_ctx* c) {
     off += align_up(npad * rb);
     L.phib = off;
     off += align_up(npad * rb);
+    L.pfield = off;
+    off += 2 * align_up(npad * rb);
     L.part = off;
     off += align_up(2 * nblk * sizeof(double));
     L.total = off;
@@ -379,6 +381,8 @@ int ld_adjoint_attach(ld_ctx* c, void* dev_workspace, size_t bytes) {
     c->adj_gmb = w + L.gmb;
     c->adj_mub = w + L.mub;
     c->adj_phib = w + L.phib;
+    c->adj_p[0] = w + L.pfield;
+    c->adj_p[1] = w + L.pfield + align_up((size_t)c->geom.npad * c->real_bytes);
     c->adj_part = (double*)(w + L.part);
     c->adj_cur = 0;
     c->adj_ready = true;

@@ -50,6 +50,7 @@ struct ld_ctx {
     void* adj_gmb;   // 3 x npad
     void* adj_mub;   // npad
     void* adj_phib;  // npad
+    void* adj_p[2];  // per-site part of gbar of each adjoint state (npad)
     double* adj_part;
     int num_sms;      // multiprocessors of the current device
     char last_error[256];
