@@ -13,6 +13,12 @@
 // of plane k is read again for the collision two planes after phi(k) read
 // it; that second read and the halo reads of neighbouring tiles are served by
 // L2. Propagation writes into the other buffer of the ping-pong pair.
+// The 16-bit storage forms keep the tile's g values of the last three planes
+// in a shared-memory ring (29 KB) as the phi pass loads them, so the
+// collision two planes later reads g from shared memory rather than again
+// from L2 or HBM (under a full machine those lines have often left L2 by
+// then). FP32 and FP64 read g again: their ring (58 KB, 117 KB) would cost
+// CTAs per SM, which measured slower.
 // Template only: instantiated per storage precision by ld_prec_f64.cu and
 // ld_prec_lp.cu.
 #pragma once
@@ -42,12 +48,16 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
                  const float* __restrict__ ref_g, typename Prec<P>::real_t* __restrict__ phi_out,
                  typename Prec<P>::real_t* __restrict__ mu_out) {
     using R = typename Prec<P>::real_t;
+    using S = typename Prec<P>::store_t;
     constexpr int PW = kTX + 4, PH = TY + 4;  // phi ring plane
     constexpr int MW = kTX + 2, MH = TY + 2;  // mu ring plane
     constexpr int NT = kTX * TY;
+    constexpr bool kKeepG = sizeof(S) == 2;
     __shared__ R phis[3][PH][PW];
     __shared__ R mus[3][MH][MW];
     __shared__ float refs[2 * Q];
+    extern __shared__ __align__(16) unsigned char keep_smem[];
+    S* gring = reinterpret_cast<S*>(keep_smem);  // [3][Q][TY][kTX], slot = phi slot of the plane
 
     const int tid = threadIdx.x;
     const int tx = tid % kTX, ty = tid / kTX;
@@ -65,9 +75,15 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
             const int hx = idx % PW, hy = idx / PW;
             const int gx = wrap_once(x0 + hx - 2, nx), gy = wrap_once(y0 + hy - 2, ny);
             const int s = zoff + gy * nx + gx;
+            const bool interior = kKeepG && hx >= 2 && hx < kTX + 2 && hy >= 2 && hy < TY + 2;
+            S* keep = gring + ((size_t)slot * Q * TY + (hy - 2)) * kTX + (hx - 2);
             R acc = R(0);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) acc += Prec<P>::decode(gs[i * npad + s], refs[Q + i]);
+            for (int i = 0; i < Q; ++i) {
+                const S v = gs[i * npad + s];
+                acc += Prec<P>::decode(v, refs[Q + i]);
+                if (interior) keep[i * (TY * kTX)] = v;
+            }
             phis[slot][hy][hx] = acc;
         }
     };
@@ -141,7 +157,10 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
 
         R gg[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) gg[i] = Prec<P>::decode(gs[i * npad + s], refs[Q + i]);
+        for (int i = 0; i < Q; ++i) {
+            const S v = kKeepG ? gring[((size_t)ps(k) * Q + i) * (TY * kTX) + ty * kTX + tx] : gs[i * npad + s];
+            gg[i] = Prec<P>::decode(v, refs[Q + i]);
+        }
         collide_g(gg, ph, muc, ux, uy, uz, m);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -179,10 +198,18 @@ template <int P>
 cudaError_t step_fused_p(ld_ctx* c, const void* src, void* dst, void* fields) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
+    constexpr size_t kRingBytes = sizeof(S) == 2 ? 3 * (size_t)Q * kTY * kTX * sizeof(S) : 0;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_fused<P, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kRingBytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
     const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
     const int zc = choose_zc(g.nx, g.ny, g.nz, c->num_sms, fused_ctas_per_sm<P>());
     const dim3 grid(g.nx / kTX, g.ny / kTY, g.nz / zc);
-    k_step_fused<P, kTY><<<grid, kTX * kTY, 0, c->stream>>>(g, model_of<R>(c->prm), zc, (const S*)f_part(c, src),
+    k_step_fused<P, kTY><<<grid, kTX * kTY, kRingBytes, c->stream>>>(g, model_of<R>(c->prm), zc, (const S*)f_part(c, src),
                                                             (const S*)g_part(c, src), (S*)f_part(c, dst),
                                                             (S*)g_part(c, dst), c->ref,
                                                             fields ? (R*)fields : nullptr,
