@@ -12,7 +12,9 @@
 // mu(k+1), then collides plane k and propagates it (push to x + c_i). The g
 // of plane k is read again for the collision two planes after phi(k) read
 // it; that second read and the halo reads of neighbouring tiles are served by
-// L2. Propagation writes into the other buffer of the ping-pong pair.
+// L2 (the phi pass loads g under an evict-last policy, the collision re-reads
+// it as evict-first). Propagation writes into the other buffer of the
+// ping-pong pair.
 // The 16-bit storage forms keep the tile's g values of the last three planes
 // in a shared-memory ring (29 KB) as the phi pass loads them, so the
 // collision two planes later reads g from shared memory rather than again
@@ -24,6 +26,7 @@
 #pragma once
 #include "ld_common.cuh"
 #include "ld_internal.h"
+#include "ld_tma.cuh"
 
 namespace ld {
 namespace {
@@ -66,6 +69,9 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     const int plane = nx * ny;
     const long long npad = g.npad;
     if (tid < 2 * Q) refs[tid] = ref_g[tid];
+    // g is read by the phi pass and, two planes later, by the collision:
+    // keep those lines in L2 until then, and release them at the second read.
+    const uint64_t keep_l2 = make_l2_evict_last_policy(), drop_l2 = make_l2_evict_first_policy();
     __syncthreads();
 
     // phi of plane zp over the tile + 2-halo, into ring slot `slot`.
@@ -80,7 +86,7 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
             R acc = R(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const S v = gs[i * npad + s];
+                const S v = ld_l2_hint(gs + i * npad + s, keep_l2);
                 acc += Prec<P>::decode(v, refs[Q + i]);
                 if (interior) keep[i * (TY * kTX)] = v;
             }
@@ -158,7 +164,8 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
         R gg[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const S v = kKeepG ? gring[((size_t)ps(k) * Q + i) * (TY * kTX) + ty * kTX + tx] : gs[i * npad + s];
+            const S v = kKeepG ? gring[((size_t)ps(k) * Q + i) * (TY * kTX) + ty * kTX + tx]
+                               : ld_l2_hint(gs + i * npad + s, drop_l2);
             gg[i] = Prec<P>::decode(v, refs[Q + i]);
         }
         collide_g(gg, ph, muc, ux, uy, uz, m);

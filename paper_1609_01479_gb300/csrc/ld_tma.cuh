@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace ld {
 
@@ -66,6 +67,34 @@ __device__ __forceinline__ uint64_t make_l2_evict_last_policy() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     return pol;
+}
+
+// L2 policy whose lines are evicted first (a value's last use).
+__device__ __forceinline__ uint64_t make_l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// Global loads with an L2 cache policy, for 32-, 16- and 64-bit storage words.
+__device__ __forceinline__ float ld_l2_hint(const float* p, uint64_t pol) {
+    float v;
+    asm("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_l2_hint(const double* p, uint64_t pol) {
+    double v;
+    asm("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+template <class T>
+__device__ __forceinline__ T ld_l2_hint(const T* p, uint64_t pol) {  // 16-bit words
+    static_assert(sizeof(T) == 2, "16-bit storage word");
+    unsigned short bits;
+    asm("ld.global.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(bits) : "l"(p), "l"(pol));
+    T v;
+    memcpy(&v, &bits, 2);
+    return v;
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
