@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     constexpr int MW = kTX + 2, MH = TY + 2;  // mu ring plane
     constexpr int NT = kTX * TY;
     constexpr bool kKeepG = sizeof(S) == 2;
+    constexpr bool kEarlyG = sizeof(S) == 4;  // FP64 has no registers to spare for it
     __shared__ R phis[3][PH][PW];
     __shared__ R mus[3][MH][MW];
     __shared__ float refs[2 * Q];
@@ -122,15 +123,29 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     const int oyp = y + 1 == ny ? (1 - ny) * nx : nx, oym = y == 0 ? (ny - 1) * nx : -nx;
 
     for (int k = z0; k < z0 + zc; ++k) {
+        const int z = k;  // zc divides nz: k < nz
+        const int s = z * plane + y * nx + x;
+        // Loads for this plane's collision issued ahead of the phi and mu
+        // passes, so that their latency overlaps that work: in FP32 the g
+        // re-read (an L2 hit), in the 16-bit forms (g kept in shared memory)
+        // f, after the phi pass's own loads. Issuing f early in FP32
+        // measured slower.
+        S gpre[Q], fpre[Q];
+        if constexpr (kEarlyG) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) gpre[i] = ld_l2_hint_now(gs + i * npad + s, drop_l2);
+        }
         __syncthreads();  // previous collision done with phi(k-1) and mu(k-2) slots
         phi_plane(k + 2, ps(k + 2));
+        if constexpr (kKeepG) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) fpre[i] = ld_l2_hint_now(fs + i * npad + s, drop_l2);
+        }
         __syncthreads();
         mu_plane(ms(k + 1), ps(k), ps(k + 1), ps(k + 2));
         __syncthreads();
 
-        const int z = k;  // zc divides nz: k < nz
         const int ozp = z + 1 == nz ? (1 - nz) * plane : plane, ozm = z == 0 ? (nz - 1) * plane : -plane;
-        const int s = z * plane + y * nx + x;
         const R ph = phis[ps(k)][ty + 2][tx + 2];
         const int mc = ms(k);
         const R muc = mus[mc][ty + 1][tx + 1];
@@ -147,7 +162,7 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
         R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            f[i] = Prec<P>::decode(fs[i * npad + s], refs[i]);
+            f[i] = Prec<P>::decode(kKeepG ? fpre[i] : fs[i * npad + s], refs[i]);
             rho += f[i];
             add_c(i, f[i], jx, jy, jz);
         }
@@ -164,8 +179,9 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
         R gg[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const S v = kKeepG ? gring[((size_t)ps(k) * Q + i) * (TY * kTX) + ty * kTX + tx]
-                               : ld_l2_hint(gs + i * npad + s, drop_l2);
+            const S v = kKeepG    ? gring[((size_t)ps(k) * Q + i) * (TY * kTX) + ty * kTX + tx]
+                        : kEarlyG ? gpre[i]
+                                  : ld_l2_hint(gs + i * npad + s, drop_l2);
             gg[i] = Prec<P>::decode(v, refs[Q + i]);
         }
         collide_g(gg, ph, muc, ux, uy, uz, m);

@@ -76,26 +76,33 @@ __device__ __forceinline__ uint64_t make_l2_evict_first_policy() {
     return pol;
 }
 
-// Global loads with an L2 cache policy, for 32-, 16- and 64-bit storage words.
-__device__ __forceinline__ float ld_l2_hint(const float* p, uint64_t pol) {
-    float v;
-    asm("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ double ld_l2_hint(const double* p, uint64_t pol) {
-    double v;
-    asm("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
-    return v;
-}
-template <class T>
-__device__ __forceinline__ T ld_l2_hint(const T* p, uint64_t pol) {  // 16-bit words
-    static_assert(sizeof(T) == 2, "16-bit storage word");
-    unsigned short bits;
-    asm("ld.global.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(bits) : "l"(p), "l"(pol));
-    T v;
-    memcpy(&v, &bits, 2);
-    return v;
-}
+// Global loads with an L2 cache policy, for 32-, 16- and 64-bit storage
+// words. The _now forms are volatile: the compiler keeps them where they are
+// written, which is how a kernel issues a load early (before a barrier) to
+// overlap its latency with other work.
+#define LD_DEFINE_L2_HINT_LOADS(NAME, QUAL)                                                        \
+    __device__ __forceinline__ float NAME(const float* p, uint64_t pol) {                          \
+        float v;                                                                                   \
+        asm QUAL("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));     \
+        return v;                                                                                  \
+    }                                                                                              \
+    __device__ __forceinline__ double NAME(const double* p, uint64_t pol) {                        \
+        double v;                                                                                  \
+        asm QUAL("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));     \
+        return v;                                                                                  \
+    }                                                                                              \
+    template <class T>                                                                             \
+    __device__ __forceinline__ T NAME(const T* p, uint64_t pol) {                                  \
+        static_assert(sizeof(T) == 2, "16-bit storage word");                                      \
+        unsigned short bits;                                                                       \
+        asm QUAL("ld.global.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(bits) : "l"(p), "l"(pol));  \
+        T v;                                                                                       \
+        memcpy(&v, &bits, 2);                                                                      \
+        return v;                                                                                  \
+    }
+LD_DEFINE_L2_HINT_LOADS(ld_l2_hint, )
+LD_DEFINE_L2_HINT_LOADS(ld_l2_hint_now, volatile)
+#undef LD_DEFINE_L2_HINT_LOADS
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
