@@ -148,8 +148,10 @@ int ld_save_state(ld_ctx* ctx, void* dev_buf);
 int ld_load_state(ld_ctx* ctx, const void* dev_buf);
 
 /* One full step from a saved state to another (both device buffers of
- * ld_state_bytes() bytes, distinct), without touching the context's own
+ * ld_state_bytes() bytes, distinct, 16-byte aligned: the step kernels move
+ * rows of the state with bulk copies), without touching the context's own
  * state: used to recompute a checkpointed segment into a tape of states.
+ * LD_EINVAL for host, equal or misaligned buffers.
  * fields_out (device, ld_fields_bytes(), or NULL) receives the phi and mu
  * fields of the source state ([phi npad][mu npad] in the arithmetic type),
  * which ld_adjoint_step can then reuse instead of recomputing them. */

@@ -396,6 +396,8 @@ int ld_step_between(ld_ctx* c, const void* src_state, void* dst_state, void* fie
     if (rc) return rc;
     if (!is_device_ptr(src_state) || !is_device_ptr(dst_state) || src_state == dst_state)
         return fail(c, LD_EINVAL, "src and dst must be distinct device state buffers");
+    if ((uintptr_t)src_state % 16 || (uintptr_t)dst_state % 16)
+        return fail(c, LD_EINVAL, "src and dst state buffers must be 16-byte aligned");
     if (!opt_device(fields_out)) return fail(c, LD_EINVAL, "fields_out must be a device pointer or NULL");
     cudaError_t e = ld::launch_step(c, src_state, dst_state, fields_out);
     if (e != cudaSuccess) return cuda_fail(c, e, "ld_step_between");

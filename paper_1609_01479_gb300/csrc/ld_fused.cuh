@@ -43,7 +43,10 @@ constexpr int fused_ctas_per_sm() {
 // Periodic image of a coordinate at most one period outside [0, n).
 __device__ __forceinline__ int wrap_once(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
-template <int P, int TY>
+// I: type of the element offsets i * npad + s. A 32-bit offset keeps the
+// 19 per-direction offsets, which the compiler holds for the whole kernel,
+// in one register each; 64-bit only where 19 npad does not fit in it.
+template <int P, int TY, class I>
 __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     k_step_fused(Geom g, Model<typename Prec<P>::real_t> m, int zc,
                  const typename Prec<P>::store_t* __restrict__ fs, const typename Prec<P>::store_t* __restrict__ gs,
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int plane = nx * ny;
-    const long long npad = g.npad;
+    const I npad = (I)g.npad;
     if (tid < 2 * Q) refs[tid] = ref_g[tid];
     // g is read by the phi pass and, two planes later, by the collision:
     // keep those lines in L2 until then, and release them at the second read.
@@ -217,14 +220,14 @@ int choose_zc(int nx, int ny, int nz, int num_sms = 152, int per_sm = 2) {
     return best;
 }
 
-template <int P>
-cudaError_t step_fused_p(ld_ctx* c, const void* src, void* dst, void* fields) {
+template <int P, class I>
+cudaError_t launch_fused(ld_ctx* c, const void* src, void* dst, void* fields) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     constexpr size_t kRingBytes = sizeof(S) == 2 ? 3 * (size_t)Q * kTY * kTX * sizeof(S) : 0;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_fused<P, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_step_fused<P, kTY, I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kRingBytes);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -232,12 +235,16 @@ cudaError_t step_fused_p(ld_ctx* c, const void* src, void* dst, void* fields) {
     const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
     const int zc = choose_zc(g.nx, g.ny, g.nz, c->num_sms, fused_ctas_per_sm<P>());
     const dim3 grid(g.nx / kTX, g.ny / kTY, g.nz / zc);
-    k_step_fused<P, kTY><<<grid, kTX * kTY, kRingBytes, c->stream>>>(g, model_of<R>(c->prm), zc, (const S*)f_part(c, src),
-                                                            (const S*)g_part(c, src), (S*)f_part(c, dst),
-                                                            (S*)g_part(c, dst), c->ref,
-                                                            fields ? (R*)fields : nullptr,
-                                                            fields ? (R*)fields + c->geom.npad : nullptr);
+    k_step_fused<P, kTY, I><<<grid, kTX * kTY, kRingBytes, c->stream>>>(
+        g, model_of<R>(c->prm), zc, (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
+        (S*)g_part(c, dst), c->ref, fields ? (R*)fields : nullptr, fields ? (R*)fields + c->geom.npad : nullptr);
     return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t step_fused_p(ld_ctx* c, const void* src, void* dst, void* fields) {
+    return (long long)Q * c->geom.npad <= 0x7fffffffLL ? launch_fused<P, int>(c, src, dst, fields)
+                                                        : launch_fused<P, long long>(c, src, dst, fields);
 }
 
 }  // namespace

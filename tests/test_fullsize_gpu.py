@@ -1,6 +1,7 @@
 """Checks at the benchmark's full size and in its launch configuration.
 
-Sampled parity at 384^3 (the spinodal benchmark lattice, fused kernel):
+Sampled parity at 384^3 (the spinodal benchmark lattice, fused kernel) and
+at 512 x 512 x 448 (large enough for the kernel's 64-bit offsets):
 after n steps the macroscopic fields at a site depend only on the initial
 state within L-infinity distance 3n + 2 of it (each step reads phi within 2
 sites for mu and grad mu, and propagation moves values by 1; the output
@@ -36,22 +37,22 @@ def ld():
     return mod
 
 
-def test_sampled_parity_384cube(ld):
-    n, steps, box = 384, 2, 24
-    phi0 = inputs.spinodal_phi(n, n, n, seed=5)
-    sim = ld.LdSim(n, n, n, precision="fp32")  # the benchmark's kernel and precision
+def _sampled_parity(ld, nx, ny, nz, samples, seed):
+    """Run 2 FP32 steps on the full lattice and compare the moments at the
+    sampled sites with the oracle on periodic 24^3 boxes around them."""
+    steps, box = 2, 24
+    phi0 = inputs.spinodal_phi(nx, ny, nz, seed=seed)
+    sim = ld.LdSim(nx, ny, nz, precision="fp32")  # the benchmark's kernel and precision
     sim.init(torch.from_numpy(phi0).cuda())
     sim.step(steps)
     m = sim.moments()
     totals = m["totals"].cpu().numpy()
-    rng = np.random.default_rng(99)
-    samples = [(0, 0, 0), (n - 1, n - 1, n - 1), (191, 7, 383)] + [tuple(rng.integers(0, n, 3)) for _ in range(5)]
     prm = oracle.param_vector()
     h = box // 2
     for (z, y, x) in samples:
-        zi = (np.arange(z - h, z + h) % n)[:, None, None]
-        yi = (np.arange(y - h, y + h) % n)[None, :, None]
-        xi = (np.arange(x - h, x + h) % n)[None, None, :]
+        zi = (np.arange(z - h, z + h) % nz)[:, None, None]
+        yi = (np.arange(y - h, y + h) % ny)[None, :, None]
+        xi = (np.arange(x - h, x + h) % nx)[None, None, :]
         sub = phi0[zi, yi, xi]
         f, g = oracle.init(sub, prm)
         f, g = oracle.step(f, g, prm, steps)
@@ -66,12 +67,30 @@ def test_sampled_parity_384cube(ld):
         assert abs(got_rho - ref_rho) < 5e-7
         assert abs(got_phi - ref_phi) < 5e-7
         assert np.abs(got_u - ref_u).max() < 5e-7
-    # conservation over the whole 384^3 lattice
+    del m
+    # conservation over the whole lattice
+    n = nx * ny * nz
     sim.init(torch.from_numpy(phi0).cuda())
     t0 = sim.totals().cpu().numpy()
-    assert abs(totals[0] - t0[0]) < 1e-6 * n ** 3
-    assert abs(totals[1] - t0[1]) < 1e-6 * n ** 3
+    assert abs(totals[0] - t0[0]) < 1e-6 * n
+    assert abs(totals[1] - t0[1]) < 1e-6 * n
     sim.close()
+
+
+def test_sampled_parity_384cube(ld):
+    n = 384
+    rng = np.random.default_rng(99)
+    samples = [(0, 0, 0), (n - 1, n - 1, n - 1), (191, 7, 383)] + [tuple(rng.integers(0, n, 3)) for _ in range(5)]
+    _sampled_parity(ld, n, n, n, samples, seed=5)
+
+
+@pytest.mark.slow
+def test_sampled_parity_64bit_offsets(ld):
+    """512 x 512 x 448 sites: 19 x npad exceeds 2^31, so the step runs the
+    kernel instance with 64-bit element offsets (35 GB of FP32 state)."""
+    nx, ny, nz = 512, 512, 448
+    samples = [(0, 0, 0), (nz - 1, ny - 1, nx - 1), (447, 3, 260), (200, 511, 0)]
+    _sampled_parity(ld, nx, ny, nz, samples, seed=6)
 
 
 def _droplet(ld, prec, n, R, steps):

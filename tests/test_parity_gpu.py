@@ -281,6 +281,14 @@ def test_errors_are_reported_not_raised_on_device(ld):
     sim.init(phi)
     sim.step(2)
     sim.check()
+    # a state buffer that is not 16-byte aligned is refused before any launch
+    nb = ld.ld_state_bytes(sim.ctx)
+    src = torch.empty(nb + 16, dtype=torch.uint8, device="cuda")
+    dst = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    ld.ld_save_state(sim.ctx, src)
+    with pytest.raises(ld.LdError) as e:
+        ld.ld_step_between(sim.ctx, src[4:], dst)
+    assert e.value.code == ld.LD_EINVAL
     f, g = sim.distributions()
     f[3, 1, 2, 3] = float("nan")
     sim.set_distributions(f, g)
