@@ -84,6 +84,52 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def fp64_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_1609_01479_gb300/csrc/ld_fused.cuh", "paper_1609_01479_gb300/csrc/ld_common.cuh",
+                "paper_1609_01479_gb300/csrc/ld_prec_f64.cu"):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_fp64_ops():
+    """FP64-pipe thread instructions per site of the FP64 fused step, from the
+    committed ncu counter summary, if taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "fp64_pipe.txt")
+    if not os.path.exists(path):
+        return None
+    want = fp64_source_hash()
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split("#")[0].split()
+            if len(parts) >= 4 and parts[0] == "k_step_fused" and parts[1] == "fp64" and parts[3] == want:
+                return float(parts[2])
+    return None
+
+
+def copy_probe_gbs(torch, nbytes=2 << 30, reps=10):
+    """Device-to-device copy bandwidth (read + write bytes / time) of a buffer
+    far larger than L2, timed with CUDA events: the achievable-bandwidth probe
+    beside the measured peak."""
+    src = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    dst = torch.empty_like(src)
+    src.fill_(1.0)
+    for _ in range(3):
+        dst.copy_(src)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        dst.copy_(src)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del src, dst
+    torch.cuda.empty_cache()
+    return 2.0 * nbytes / (ms * 1e-3) / 1e9
+
+
 def recorded_traffic(precision, size):
     """DRAM bytes per launch of the fused step from the committed ncu summary,
     if it was taken on the current kernel source."""
@@ -424,6 +470,20 @@ def main():
 
     primary = precisions[0]
     P = results[primary]
+    if "fp64" in results:
+        # FP64 is bounded by the FP64 pipe: 2 FP64 instructions per clock per SM
+        # (GB300: 1.25 TFLOP/s nominal FP64 with an FMA counted as 2 flops, at
+        # 152 SMs x 2.07 GHz), times the SMs and the maximum SM clock seen.
+        ops = recorded_fp64_ops()
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        mhz = (P["clocks"] or {}).get("sm_max_mhz") or 2070.0
+        peak_ops = 2.0 * sms * mhz * 1e6 / 1e9
+        R64 = results["fp64"]
+        achieved = None if ops is None else R64["mlups"] * 1e6 * ops / 1e9
+        R64["alu"] = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "G FP64 inst/s",
+                      "frac": None if achieved is None else achieved / peak_ops, "fp64_inst_per_site": ops,
+                      "peak_source": f"derived: 2 FP64 inst/clk/SM x {sms} SMs x {mhz:.0f} MHz"}
+    probe = copy_probe_gbs(torch) if rank == 0 else None
     e2e = None
     if not args.no_e2e:
         phi_pinned = torch.from_numpy(phi_np).pin_memory()
@@ -458,7 +518,8 @@ def main():
                      "frac": P["roofline_frac"], "traffic": traffic,
                      "kernel": "k_step_fused", "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
-                     "per_site_bytes": P["bytes_per_site"], "kernel_ms": P["kernel_ms"]},
+                     "per_site_bytes": P["bytes_per_site"], "kernel_ms": P["kernel_ms"],
+                     "copy_probe_gbs": probe, "frac_of_copy_probe": None if not probe else P["algorithmic_gbs"] / probe},
         "clocks": P["clocks"],
         "e2e": e2e,
         "gpu_launches": args.steps + 2,
