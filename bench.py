@@ -86,7 +86,7 @@ def kernel_source_hash():
 
 def fp64_source_hash():
     h = hashlib.sha256()
-    for rel in ("paper_1609_01479_gb300/csrc/ld_fused.cuh", "paper_1609_01479_gb300/csrc/ld_common.cuh",
+    for rel in ("paper_1609_01479_gb300/csrc/ld_generic.cuh", "paper_1609_01479_gb300/csrc/ld_common.cuh",
                 "paper_1609_01479_gb300/csrc/ld_prec_f64.cu"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
@@ -94,8 +94,9 @@ def fp64_source_hash():
 
 
 def recorded_fp64_ops():
-    """FP64-pipe thread instructions per site of the FP64 fused step, from the
-    committed ncu counter summary, if taken on the current source."""
+    """FP64-pipe thread instructions per site of the FP64 step (the generic
+    launches, which the library picks for FP64), from the committed ncu
+    counter summary, if taken on the current source."""
     path = os.path.join(ROOT, "profiles", "fp64_pipe.txt")
     if not os.path.exists(path):
         return None
@@ -103,7 +104,7 @@ def recorded_fp64_ops():
     with open(path) as fh:
         for line in fh:
             parts = line.split("#")[0].split()
-            if len(parts) >= 4 and parts[0] == "k_step_fused" and parts[1] == "fp64" and parts[3] == want:
+            if len(parts) >= 4 and parts[0] == "generic" and parts[1] == "fp64" and parts[3] == want:
                 return float(parts[2])
     return None
 

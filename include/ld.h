@@ -60,7 +60,9 @@ enum { LD_FP64 = 0, LD_FP32 = 1, LD_FP16DEV = 2, LD_BF16DEV = 3 };
  * LD_KERNEL_FUSED_TMA: the fused step with each plane's distributions staged
  *   in shared memory by TMA bulk copies; FP32 and the 16-bit forms only
  *   (nx % 32 == 0, ny % 8 == 0, nz % 4 == 0).
- * LD_KERNEL_AUTO: FUSED when the lattice admits it, else GENERIC. */
+ * LD_KERNEL_AUTO: FUSED when the lattice admits it, else GENERIC; always
+ * GENERIC for LD_FP64, which is bound by the FP64 pipe, where the generic
+ * launches do less FP64 work per site (no halo phi sums). */
 enum { LD_KERNEL_AUTO = 0, LD_KERNEL_GENERIC = 1, LD_KERNEL_FUSED = 2, LD_KERNEL_FUSED_TMA = 3 };
 
 enum {

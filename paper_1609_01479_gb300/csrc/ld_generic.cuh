@@ -1,6 +1,6 @@
 // Generic kernels: any lattice size >= 4 in every dimension, one thread per
-// site. The step runs as three launches -- phi (zeroth moment of g),
-// mu (7-point stencil), and collide+propagate -- and the same file holds the
+// site. The step runs as three launches in site order -- phi (zeroth moment
+// of g), mu (7-point stencil), and collide+propagate -- and the same file holds the
 // initialiser, the macroscopic output, the FP64 conservation sums, the
 // codec I/O and propagation alone. Templates only: instantiated per storage
 // precision by ld_prec_f64.cu and ld_prec_lp.cu.
@@ -34,62 +34,111 @@ __device__ __forceinline__ int step_coord(int a, int d, int n) {
 }
 
 // ---------------------------------------------------------------------------
-// Step, stage 1: phi = sum_i g_i (pre-collision state is stored locally).
-template <int P>
-__global__ void __launch_bounds__(kThreads) k_phi(Geom g, const typename Prec<P>::store_t* __restrict__ gs,
-                                                  const float* __restrict__ ref,
-                                                  typename Prec<P>::real_t* __restrict__ phi) {
+// The step as three launches in site order, one thread per site, each block
+// a segment of kRowThreads sites of one x-row (row r = y + ny z; a block never
+// straddles two rows, so the coordinates need one division per thread).
+// Consecutive blocks cover consecutive addresses of every stream, the order
+// that lets HBM run at its copy rate. Element offsets i npad + s are of type
+// I: 32-bit where 19 npad fits.
+constexpr int kRowThreads = 128;
+
+struct RowGeom {
+    int nx, ny, nz, nchunks;  // nchunks = blocks per row
+};
+
+inline RowGeom row_geom(const GeomH& h) {
+    return RowGeom{h.nx, h.ny, h.nz, (h.nx + kRowThreads - 1) / kRowThreads};
+}
+
+inline unsigned row_blocks(const GeomH& h) {
+    return (unsigned)((long long)h.ny * h.nz * ((h.nx + kRowThreads - 1) / kRowThreads));
+}
+
+// Site of this thread in row segment b (false past the end of its row).
+__device__ __forceinline__ bool row_site(const RowGeom& rg, int b, int& x, int& y, int& z, int& s) {
+    const int r = b / rg.nchunks;
+    x = (b - r * rg.nchunks) * kRowThreads + threadIdx.x;
+    y = r % rg.ny;
+    z = r / rg.ny;
+    s = r * rg.nx + x;
+    return x < rg.nx;
+}
+
+// Stage 1: phi = sum_i g_i (the stored state is the post-propagation one).
+template <int P, class I>
+__global__ void __launch_bounds__(kRowThreads) k_phi(RowGeom rg, I npad, const typename Prec<P>::store_t* __restrict__ gs,
+                                                     const float* __restrict__ ref,
+                                                     typename Prec<P>::real_t* __restrict__ phi) {
     using R = typename Prec<P>::real_t;
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.n) return;
+    int x, y, z, s;
+    if (!row_site(rg, blockIdx.x, x, y, z, s)) return;
     R acc = R(0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) acc += Prec<P>::decode(gs[i * g.npad + s], ref[Q + i]);
+    for (int i = 0; i < Q; ++i) acc += Prec<P>::decode(gs[i * npad + s], ref[Q + i]);
     phi[s] = acc;
 }
 
-// Step, stage 2: mu = A phi + B phi^3 - kappa lap(phi).
+// Stage 2: mu = A phi + B phi^3 - kappa lap(phi), 7-point Laplacian.
 template <class R>
-__global__ void __launch_bounds__(kThreads) k_mu(Geom g, Model<R> m, const R* __restrict__ phi,
-                                                 R* __restrict__ mu) {
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.n) return;
-    int x, y, z;
-    site_coords(g, s, x, y, z);
-    const R nb = phi[site_of(g, wrap_inc(x, g.nx), y, z)] + phi[site_of(g, wrap_dec(x, g.nx), y, z)]
-               + phi[site_of(g, x, wrap_inc(y, g.ny), z)] + phi[site_of(g, x, wrap_dec(y, g.ny), z)]
-               + phi[site_of(g, x, y, wrap_inc(z, g.nz))] + phi[site_of(g, x, y, wrap_dec(z, g.nz))];
+__global__ void __launch_bounds__(kRowThreads) k_mu(RowGeom rg, Model<R> m, const R* __restrict__ phi,
+                                                    R* __restrict__ mu) {
+    int x, y, z, s;
+    if (!row_site(rg, blockIdx.x, x, y, z, s)) return;
+    const int nx = rg.nx, plane = rg.nx * rg.ny;
+    const int xp = x + 1 == nx ? 1 - nx : 1, xm = x == 0 ? nx - 1 : -1;
+    const int yp = y + 1 == rg.ny ? (1 - rg.ny) * nx : nx, ym = y == 0 ? (rg.ny - 1) * nx : -nx;
+    const int zp = z + 1 == rg.nz ? (1 - rg.nz) * plane : plane, zm = z == 0 ? (rg.nz - 1) * plane : -plane;
+    const R nb = phi[s + xp] + phi[s + xm] + phi[s + yp] + phi[s + ym] + phi[s + zp] + phi[s + zm];
     mu[s] = chem_potential(phi[s], nb, m);
 }
 
-// Step, stage 3: force, velocity, collisions of f and g, and propagation
-// (push: the post-collision value of direction i goes to x + c_i).
+// Resident blocks per SM the collision kernel is compiled for: 6 x 128
+// threads (80 registers) with FP32 arithmetic, 3 with FP64.
 template <int P>
-__global__ void __launch_bounds__(kThreads)
-    k_collide(Geom g, Model<typename Prec<P>::real_t> m, const typename Prec<P>::store_t* __restrict__ fs,
+constexpr int rows_blocks_per_sm() {
+    return sizeof(typename Prec<P>::real_t) == 4 ? 6 : 3;
+}
+
+// Stage 3: force, velocity, collisions of f and g, and propagation (push: the
+// post-collision value of direction i goes to x + c_i) with streaming stores.
+template <int P, class I>
+__global__ void __launch_bounds__(kRowThreads, rows_blocks_per_sm<P>())
+    k_collide(RowGeom rg, I npad, Model<typename Prec<P>::real_t> m, const typename Prec<P>::store_t* __restrict__ fs,
               const typename Prec<P>::store_t* __restrict__ gs, typename Prec<P>::store_t* __restrict__ fd,
               typename Prec<P>::store_t* __restrict__ gd, const typename Prec<P>::real_t* __restrict__ phi,
               const typename Prec<P>::real_t* __restrict__ mu, const float* __restrict__ ref) {
     using R = typename Prec<P>::real_t;
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.n) return;
-    int x, y, z;
-    site_coords(g, s, x, y, z);
-    const int xp = wrap_inc(x, g.nx), xm = wrap_dec(x, g.nx);
-    const int yp = wrap_inc(y, g.ny), ym = wrap_dec(y, g.ny);
-    const int zp = wrap_inc(z, g.nz), zm = wrap_dec(z, g.nz);
+    using S = typename Prec<P>::store_t;
+    __shared__ float refs[2 * Q];  // codec references, read once per block
+    if (threadIdx.x < 2 * Q) refs[threadIdx.x] = ref[threadIdx.x];
+    __syncthreads();
+    int x, y, z, s;
+    if (!row_site(rg, blockIdx.x, x, y, z, s)) return;
+    // FP32 and FP64 issue all 38 loads first; the 16-bit forms issue g after
+    // the f stores (each 16-bit value held early would take a register).
+    constexpr bool kEarlyG = sizeof(S) >= 4;
+    S fr[Q], gr[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        fr[i] = __ldcs(fs + i * npad + s);
+        if (kEarlyG) gr[i] = __ldcs(gs + i * npad + s);
+    }
+    const int nx = rg.nx, plane = rg.nx * rg.ny;
+    const int oxp = x + 1 == nx ? 1 - nx : 1, oxm = x == 0 ? nx - 1 : -1;
+    const int oyp = y + 1 == rg.ny ? (1 - rg.ny) * nx : nx, oym = y == 0 ? (rg.ny - 1) * nx : -nx;
+    const int ozp = z + 1 == rg.nz ? (1 - rg.nz) * plane : plane, ozm = z == 0 ? (rg.nz - 1) * plane : -plane;
 
-    const R ph = phi[s];
-    const R gmx = R(0.5) * (mu[site_of(g, xp, y, z)] - mu[site_of(g, xm, y, z)]);
-    const R gmy = R(0.5) * (mu[site_of(g, x, yp, z)] - mu[site_of(g, x, ym, z)]);
-    const R gmz = R(0.5) * (mu[site_of(g, x, y, zp)] - mu[site_of(g, x, y, zm)]);
+    const R ph = phi[s], muc = mu[s];
+    const R gmx = R(0.5) * (mu[s + oxp] - mu[s + oxm]);
+    const R gmy = R(0.5) * (mu[s + oyp] - mu[s + oym]);
+    const R gmz = R(0.5) * (mu[s + ozp] - mu[s + ozm]);
     const R Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
 
     R f[Q];
     R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        f[i] = Prec<P>::decode(fs[i * g.npad + s], ref[i]);
+        f[i] = Prec<P>::decode(fr[i], refs[i]);
         rho += f[i];
         add_c(i, f[i], jx, jy, jz);
     }
@@ -98,20 +147,19 @@ __global__ void __launch_bounds__(kThreads)
     collide_f(f, rho, ux, uy, uz, Fx, Fy, Fz, m);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const long long d = site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny),
-                                    step_coord(z, cz(i), g.nz));
-        fd[i * g.npad + d] = Prec<P>::encode(f[i], ref[i]);
+        const int d = s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
+                      (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
+        __stcs(fd + i * npad + d, Prec<P>::encode(f[i], refs[i]));
     }
-
     R gg[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) gg[i] = Prec<P>::decode(gs[i * g.npad + s], ref[Q + i]);
-    collide_g(gg, ph, mu[s], ux, uy, uz, m);
+    for (int i = 0; i < Q; ++i) gg[i] = Prec<P>::decode(kEarlyG ? gr[i] : __ldcs(gs + i * npad + s), refs[Q + i]);
+    collide_g(gg, ph, muc, ux, uy, uz, m);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const long long d = site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny),
-                                    step_coord(z, cz(i), g.nz));
-        gd[i * g.npad + d] = Prec<P>::encode(gg[i], ref[Q + i]);
+        const int d = s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
+                      (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
+        __stcs(gd + i * npad + d, Prec<P>::encode(gg[i], refs[Q + i]));
     }
 }
 
@@ -356,31 +404,44 @@ cudaError_t init_p(ld_ctx* c, const double* phi, const double* rho, const double
 
 // phi and mu of a state into `fields` ([phi npad][mu npad]), or into the
 // context's scratch when fields is null.
-template <int P>
-cudaError_t phi_mu_p(ld_ctx* c, const void* state, void* fields = nullptr) {
+template <int P, class I>
+cudaError_t phi_mu_rows(ld_ctx* c, const void* state, void* fields) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
-    const Geom g = to_dev(c->geom);
+    const RowGeom rg = row_geom(c->geom);
+    const unsigned nb = row_blocks(c->geom);
     R* phi = fields ? (R*)fields : (R*)c->phi;
-    R* mu = fields ? (R*)fields + g.npad : (R*)c->mu;
-    k_phi<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, (const S*)g_part(c, state), c->ref, phi);
-    k_mu<R><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, model_of<R>(c->prm), phi, mu);
+    R* mu = fields ? (R*)fields + c->geom.npad : (R*)c->mu;
+    k_phi<P, I><<<nb, kRowThreads, 0, c->stream>>>(rg, (I)c->geom.npad, (const S*)g_part(c, state), c->ref, phi);
+    k_mu<R><<<nb, kRowThreads, 0, c->stream>>>(rg, model_of<R>(c->prm), phi, mu);
+    return cudaGetLastError();
+}
+
+inline bool offsets_fit_int(const ld_ctx* c) { return (long long)Q * c->geom.npad <= 0x7fffffffLL; }
+
+template <int P>
+cudaError_t phi_mu_p(ld_ctx* c, const void* state, void* fields = nullptr) {
+    return offsets_fit_int(c) ? phi_mu_rows<P, int>(c, state, fields) : phi_mu_rows<P, long long>(c, state, fields);
+}
+
+template <int P, class I>
+cudaError_t collide_rows(ld_ctx* c, const void* src, void* dst, void* fields) {
+    using S = typename Prec<P>::store_t;
+    using R = typename Prec<P>::real_t;
+    cudaError_t e = phi_mu_rows<P, I>(c, src, fields);
+    if (e != cudaSuccess) return e;
+    const R* phi = fields ? (const R*)fields : (const R*)c->phi;
+    const R* mu = fields ? (const R*)fields + c->geom.npad : (const R*)c->mu;
+    k_collide<P, I><<<row_blocks(c->geom), kRowThreads, 0, c->stream>>>(
+        row_geom(c->geom), (I)c->geom.npad, model_of<R>(c->prm), (const S*)f_part(c, src), (const S*)g_part(c, src),
+        (S*)f_part(c, dst), (S*)g_part(c, dst), phi, mu, c->ref);
     return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t collide_p(ld_ctx* c, const void* src, void* dst, void* fields) {
-    using S = typename Prec<P>::store_t;
-    using R = typename Prec<P>::real_t;
-    const Geom g = to_dev(c->geom);
-    cudaError_t e = phi_mu_p<P>(c, src, fields);
-    if (e != cudaSuccess) return e;
-    const R* phi = fields ? (const R*)fields : (const R*)c->phi;
-    const R* mu = fields ? (const R*)fields + g.npad : (const R*)c->mu;
-    k_collide<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(
-        g, model_of<R>(c->prm), (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
-        (S*)g_part(c, dst), phi, mu, c->ref);
-    return cudaGetLastError();
+    return offsets_fit_int(c) ? collide_rows<P, int>(c, src, dst, fields)
+                              : collide_rows<P, long long>(c, src, dst, fields);
 }
 
 template <int P>

@@ -69,7 +69,9 @@ int choose_step_kernel(int nx, int ny, int nz, int prec, int requested) {
         case LD_KERNEL_GENERIC: return kStepGeneric;
         case LD_KERNEL_FUSED: return regs ? kStepRegs : 0;
         case LD_KERNEL_FUSED_TMA: return tma ? kStepTma : 0;
-        case LD_KERNEL_AUTO: return regs ? kStepRegs : kStepGeneric;
+        // FP64 is bound by the FP64 pipe, and the three row-ordered launches
+        // do less FP64 work per site than the fused step (no halo phi sums)
+        case LD_KERNEL_AUTO: return regs && !f64p ? kStepRegs : kStepGeneric;
         default: return 0;
     }
 }
