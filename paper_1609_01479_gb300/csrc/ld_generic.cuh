@@ -35,13 +35,11 @@ __device__ __forceinline__ int step_coord(int a, int d, int n) {
 
 // ---------------------------------------------------------------------------
 // The step as three launches in site order, one thread per site, each block
-// a segment of kRowThreads sites of one x-row (row r = y + ny z; a block never
-// straddles two rows, so the coordinates need one division per thread).
+// a segment of kRowThreads sites of one x-row (a block never straddles two
+// rows, so the coordinates need one division per thread).
 // Consecutive blocks cover consecutive addresses of every stream, the order
 // that lets HBM run at its copy rate. Element offsets i npad + s are of type
 // I: 32-bit where 19 npad fits.
-constexpr int kRowThreads = 128;
-
 struct RowGeom {
     int nx, ny, nz, nchunks;  // nchunks = blocks per row
 };
@@ -50,9 +48,7 @@ inline RowGeom row_geom(const GeomH& h) {
     return RowGeom{h.nx, h.ny, h.nz, (h.nx + kRowThreads - 1) / kRowThreads};
 }
 
-inline unsigned row_blocks(const GeomH& h) {
-    return (unsigned)((long long)h.ny * h.nz * ((h.nx + kRowThreads - 1) / kRowThreads));
-}
+inline unsigned row_blocks(const GeomH& h) { return (unsigned)row_segments(h); }
 
 // Site of this thread in row segment b (false past the end of its row).
 __device__ __forceinline__ bool row_site(const RowGeom& rg, int b, int& x, int& y, int& z, int& s) {

@@ -14,6 +14,13 @@ struct GeomH {
     long long n, npad;
 };
 
+// Row-ordered launches: one block per segment of kRowThreads sites of one
+// x-row (row r = y + ny z), so consecutive blocks cover consecutive addresses.
+constexpr int kRowThreads = 128;
+inline long long row_segments(const GeomH& g) {
+    return (long long)g.ny * g.nz * ((g.nx + kRowThreads - 1) / kRowThreads);
+}
+
 // Fixed reduction grid: per-block partials then one ordered final pass, so
 // every FP64 sum is bitwise reproducible.
 constexpr int kRedBlocks = 1024;

@@ -37,12 +37,12 @@ def ld():
     return mod
 
 
-def _sampled_parity(ld, nx, ny, nz, samples, seed):
+def _sampled_parity(ld, nx, ny, nz, samples, seed, kernel="auto"):
     """Run 2 FP32 steps on the full lattice and compare the moments at the
     sampled sites with the oracle on periodic 24^3 boxes around them."""
     steps, box = 2, 24
     phi0 = inputs.spinodal_phi(nx, ny, nz, seed=seed)
-    sim = ld.LdSim(nx, ny, nz, precision="fp32")  # the benchmark's kernel and precision
+    sim = ld.LdSim(nx, ny, nz, precision="fp32", kernel=kernel)  # auto: the benchmark's kernel
     sim.init(torch.from_numpy(phi0).cuda())
     sim.step(steps)
     m = sim.moments()
@@ -85,12 +85,13 @@ def test_sampled_parity_384cube(ld):
 
 
 @pytest.mark.slow
-def test_sampled_parity_64bit_offsets(ld):
+@pytest.mark.parametrize("kernel", ["fused", "generic"])
+def test_sampled_parity_64bit_offsets(ld, kernel):
     """512 x 512 x 448 sites: 19 x npad exceeds 2^31, so the step runs the
-    kernel instance with 64-bit element offsets (35 GB of FP32 state)."""
+    kernel instances with 64-bit element offsets (35 GB of FP32 state)."""
     nx, ny, nz = 512, 512, 448
     samples = [(0, 0, 0), (nz - 1, ny - 1, nx - 1), (447, 3, 260), (200, 511, 0)]
-    _sampled_parity(ld, nx, ny, nz, samples, seed=6)
+    _sampled_parity(ld, nx, ny, nz, samples, seed=6, kernel=kernel)
 
 
 def _droplet(ld, prec, n, R, steps):
