@@ -8,7 +8,8 @@ The arithmetic lives in ``ld_oracle.cpp`` (plain double, ``-ffp-contract=off``)
 and follows the components of one Ludwig timestep named in Sec. 2.1.1 of the
 paper (Collision, Propagation, Chemical stress, Order Parameter Gradients) in
 their binary-fluid form: D3Q19 BGK with Guo forcing, the g collision, the
-7-point Laplacian and central-difference force, and periodic propagation.
+7-point Laplacian and central-difference force (or their 19-point isotropic
+forms, ``stencil=19``), and periodic propagation.
 This module only marshals numpy arrays through ctypes and builds the shared
 object with g++.
 """
@@ -29,9 +30,12 @@ _lock = threading.Lock()
 _lib = None
 
 Q = 19
-# Parameter vector order used by every call.
-PARAM_NAMES = ("A", "B", "kappa", "Gamma", "tau_f", "tau_g", "rho0")
-DEFAULT_PARAMS = dict(A=-0.0625, B=0.0625, kappa=0.04, Gamma=0.5, tau_f=1.0, tau_g=1.0, rho0=1.0)
+# Parameter vector order used by every call; the last entry selects the
+# stencils (0: 7-point Laplacian and central difference, 1: 19-point
+# isotropic). Derivative directions cover the first seven.
+PARAM_NAMES = ("A", "B", "kappa", "Gamma", "tau_f", "tau_g", "rho0", "stencil")
+DEFAULT_PARAMS = dict(A=-0.0625, B=0.0625, kappa=0.04, Gamma=0.5, tau_f=1.0, tau_g=1.0, rho0=1.0, stencil=0.0)
+STENCILS = {7: 0.0, 19: 1.0}
 
 
 def build(force: bool = False) -> str:
@@ -64,8 +68,8 @@ def _load():
         lib.orc_feq.argtypes = [ctypes.c_double, P, P]
         lib.orc_geq.argtypes = [ctypes.c_double, P, ctypes.c_double, ctypes.c_double, P]
         lib.orc_guo.argtypes = [P, P, ctypes.c_double, P]
-        lib.orc_laplacian.argtypes = [i, i, i, P, P]
-        lib.orc_gradient.argtypes = [i, i, i, P, P]
+        lib.orc_laplacian.argtypes = [i, i, i, i, P, P]
+        lib.orc_gradient.argtypes = [i, i, i, i, P, P]
         lib.orc_propagate.argtypes = [i, i, i, i, P, P]
         lib.orc_init.argtypes = [i, i, i, P, P, P, P, P, P]
         lib.orc_step.argtypes = [i, i, i, P, P, P, i]
@@ -90,17 +94,28 @@ def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _prm(p):
+    """The 8-entry parameter vector the C side reads (a 7-entry one gets the
+    default stencil)."""
+    p = _f64(p)
+    if p.shape == (7,):
+        p = np.concatenate([p, [0.0]])
+    assert p.shape == (8,), "parameter vector: A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil"
+    return p
+
+
 def _check(rc, what):
     if rc != 0:
         raise ValueError(f"oracle {what} rejected its arguments (rc={rc})")
 
 
 def param_vector(**overrides) -> np.ndarray:
+    """Parameter vector; ``stencil`` is given as 7 or 19."""
     p = dict(DEFAULT_PARAMS)
     for k, v in overrides.items():
         if k not in p:
             raise KeyError(k)
-        p[k] = float(v)
+        p[k] = STENCILS[int(v)] if k == "stencil" else float(v)
     return np.array([p[k] for k in PARAM_NAMES], dtype=np.float64)
 
 
@@ -139,21 +154,22 @@ def guo(u, F, tau):
     return out
 
 
-def laplacian(phi):
-    """7-point periodic Laplacian of a (nz, ny, nx) field."""
+def laplacian(phi, stencil=7):
+    """Periodic Laplacian of a (nz, ny, nx) field: 7-point or 19-point isotropic."""
     phi = _f64(phi)
     nz, ny, nx = phi.shape
     out = np.zeros_like(phi)
-    _check(_load().orc_laplacian(nx, ny, nz, _ptr(phi), _ptr(out)), "laplacian")
+    _check(_load().orc_laplacian(nx, ny, nz, int(STENCILS[stencil]), _ptr(phi), _ptr(out)), "laplacian")
     return out
 
 
-def gradient(h):
-    """Central-difference gradient of a (nz, ny, nx) field -> (3, nz, ny, nx)."""
+def gradient(h, stencil=7):
+    """Periodic gradient of a (nz, ny, nx) field -> (3, nz, ny, nx): central
+    difference (7) or the 19-point isotropic form (19)."""
     h = _f64(h)
     nz, ny, nx = h.shape
     out = np.zeros((3,) + h.shape)
-    _check(_load().orc_gradient(nx, ny, nz, _ptr(h), _ptr(out)), "gradient")
+    _check(_load().orc_gradient(nx, ny, nz, int(STENCILS[stencil]), _ptr(h), _ptr(out)), "gradient")
     return out
 
 
@@ -172,7 +188,7 @@ def init(phi, prm, rho=None, u=None):
     nz, ny, nx = phi.shape
     f = np.zeros((Q,) + phi.shape)
     g = np.zeros((Q,) + phi.shape)
-    _check(_load().orc_init(nx, ny, nz, _ptr(_f64(prm)), _ptr(phi), _ptr(_f64(rho)), _ptr(_f64(u)),
+    _check(_load().orc_init(nx, ny, nz, _ptr(_prm(prm)), _ptr(phi), _ptr(_f64(rho)), _ptr(_f64(u)),
                             _ptr(f), _ptr(g)), "init")
     return f, g
 
@@ -182,7 +198,7 @@ def step(f, g, prm, nsteps=1):
     f = np.array(f, dtype=np.float64, order="C", copy=True)
     g = np.array(g, dtype=np.float64, order="C", copy=True)
     _, nz, ny, nx = f.shape
-    _check(_load().orc_step(nx, ny, nz, _ptr(_f64(prm)), _ptr(f), _ptr(g), int(nsteps)), "step")
+    _check(_load().orc_step(nx, ny, nz, _ptr(_prm(prm)), _ptr(f), _ptr(g), int(nsteps)), "step")
     return f, g
 
 
@@ -199,7 +215,7 @@ def macros(f, g, prm):
     out = dict(rho=np.zeros(shp), u=np.zeros((3,) + shp), phi=np.zeros(shp),
                grad_phi=np.zeros((3,) + shp), mu=np.zeros(shp), force=np.zeros((3,) + shp),
                totals=np.zeros(5))
-    _check(_load().orc_macros(nx, ny, nz, _ptr(_f64(prm)), _ptr(f), _ptr(g), _ptr(out["rho"]),
+    _check(_load().orc_macros(nx, ny, nz, _ptr(_prm(prm)), _ptr(f), _ptr(g), _ptr(out["rho"]),
                               _ptr(out["u"]), _ptr(out["phi"]), _ptr(out["grad_phi"]),
                               _ptr(out["mu"]), _ptr(out["force"]), _ptr(out["totals"])), "macros")
     return out
@@ -209,7 +225,7 @@ def step_tl(f, g, df, dg, prm, dprm, nsteps=1):
     """Tangent-linear step: returns (f, g, df, dg) after nsteps."""
     arrs = [np.array(a, dtype=np.float64, order="C", copy=True) for a in (f, g, df, dg)]
     _, nz, ny, nx = arrs[0].shape
-    _check(_load().orc_step_tl(nx, ny, nz, _ptr(_f64(prm)), _ptr(_f64(dprm)), *[_ptr(a) for a in arrs],
+    _check(_load().orc_step_tl(nx, ny, nz, _ptr(_prm(prm)), _ptr(_f64(dprm)[:7].copy()), *[_ptr(a) for a in arrs],
                                int(nsteps)), "step_tl")
     return tuple(arrs)
 
@@ -219,10 +235,10 @@ def loss_jvp(phi0, phi_target, prm, nsteps, dphi0=None, dprm=None):
     its directional derivative along (dphi0, dprm)."""
     phi0 = _f64(phi0)
     nz, ny, nx = phi0.shape
-    dprm = np.zeros(7) if dprm is None else _f64(dprm)
+    dprm = np.zeros(7) if dprm is None else _f64(dprm)[:7].copy()
     loss = np.zeros(1)
     dloss = np.zeros(1)
-    _check(_load().orc_loss_jvp(nx, ny, nz, _ptr(_f64(prm)), _ptr(dprm), _ptr(phi0), _ptr(_f64(dphi0)),
+    _check(_load().orc_loss_jvp(nx, ny, nz, _ptr(_prm(prm)), _ptr(dprm), _ptr(phi0), _ptr(_f64(dphi0)),
                                 _ptr(_f64(phi_target)), int(nsteps), _ptr(loss), _ptr(dloss)), "loss_jvp")
     return float(loss[0]), float(dloss[0])
 

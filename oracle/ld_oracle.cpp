@@ -17,8 +17,12 @@
 //   * BGK collision of g towards an equilibrium whose zeroth, first and second
 //     moments are phi, phi*u and Gamma*mu*I + phi*u*u;
 //   * the symmetric phi^4 free energy: mu = A phi + B phi^3 - kappa lap(phi),
-//     lap the 7-point Laplacian, force F = -phi * grad(mu), grad the 2-point
-//     central difference;
+//     force F = -phi * grad(mu), with one of two stencil pairs: the 7-point
+//     Laplacian and the 2-point central difference (the default), or the
+//     19-point isotropic forms on the D3Q19 neighbourhood,
+//       lap h = sum_i 6 w_i (h(x + c_i) - h(x)),
+//       grad h = sum_i 3 w_i c_i h(x + c_i),
+//     whose leading truncation errors are isotropic (sum_i w_i c c c c is);
 //   * propagation: f_i(x + c_i, t+1) = f*_i(x, t) on a periodic lattice.
 // One step is: moments -> phi stencil and mu -> force and velocity ->
 // collide f -> collide g -> propagate, all stencils on fields of the same
@@ -93,6 +97,7 @@ inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
 template <class T>
 struct Params {
     T A, B, kappa, Gamma, tau_f, tau_g, rho0;
+    int stencil;  // 0: 7-point / central difference; 1: 19-point isotropic
 };
 
 struct Lattice {
@@ -149,39 +154,70 @@ void guo_site(const T u[3], const T F[3], T tau, T out[kQ]) {
     }
 }
 
-// 7-point Laplacian, periodic.
+// Coefficients of the 19-point isotropic forms, 6 w_i and 3 w_i, written as
+// the exact fractions they are: 1/3 and 1/6 (axis neighbours), 1/6 and 1/12
+// (face diagonals).
+double lap19_coef(int i) { return i <= 6 ? 1.0 / 3.0 : 1.0 / 6.0; }
+double grad19_coef(int i) { return i <= 6 ? 1.0 / 6.0 : 1.0 / 12.0; }
+
+// Laplacian, periodic: 7-point (sum of the six axis neighbours minus 6 h), or
+// 19-point isotropic (sum over i = 1..18, in velocity order, of
+// 6 w_i (h(x + c_i) - h(x))).
 template <class T>
-void laplacian(const Lattice& L, const T* phi, T* lap) {
+void laplacian(const Lattice& L, const T* phi, T* lap, int stencil = 0) {
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < L.nz; ++z)
         for (int y = 0; y < L.ny; ++y)
             for (int x = 0; x < L.nx; ++x) {
                 long s = L.site(x, y, z);
-                T sum = phi[L.shifted(x, y, z, 1, 0, 0)] + phi[L.shifted(x, y, z, -1, 0, 0)]
-                      + phi[L.shifted(x, y, z, 0, 1, 0)] + phi[L.shifted(x, y, z, 0, -1, 0)]
-                      + phi[L.shifted(x, y, z, 0, 0, 1)] + phi[L.shifted(x, y, z, 0, 0, -1)];
-                lap[s] = sum - 6.0 * phi[s];
+                if (stencil == 0) {
+                    T sum = phi[L.shifted(x, y, z, 1, 0, 0)] + phi[L.shifted(x, y, z, -1, 0, 0)]
+                          + phi[L.shifted(x, y, z, 0, 1, 0)] + phi[L.shifted(x, y, z, 0, -1, 0)]
+                          + phi[L.shifted(x, y, z, 0, 0, 1)] + phi[L.shifted(x, y, z, 0, 0, -1)];
+                    lap[s] = sum - 6.0 * phi[s];
+                } else {
+                    T sum = 0.0;
+                    for (int i = 1; i < kQ; ++i)
+                        sum += lap19_coef(i) * (phi[L.shifted(x, y, z, kCx[i], kCy[i], kCz[i])] - phi[s]);
+                    lap[s] = sum;
+                }
             }
 }
 
-// Central difference (h(x+e_a) - h(x-e_a))/2 for a = x, y, z, periodic.
+// Gradient, periodic: central difference (h(x+e_a) - h(x-e_a))/2, or the
+// 19-point isotropic sum over i = 1..18 (velocity order, terms with c_ia = 0
+// left out) of 3 w_i c_ia h(x + c_i).
 template <class T>
-void gradient(const Lattice& L, const T* h, T* grad) {
+void gradient(const Lattice& L, const T* h, T* grad, int stencil = 0) {
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < L.nz; ++z)
         for (int y = 0; y < L.ny; ++y)
             for (int x = 0; x < L.nx; ++x) {
                 long s = L.site(x, y, z);
-                grad[0 * L.n + s] = (h[L.shifted(x, y, z, 1, 0, 0)] - h[L.shifted(x, y, z, -1, 0, 0)]) / 2.0;
-                grad[1 * L.n + s] = (h[L.shifted(x, y, z, 0, 1, 0)] - h[L.shifted(x, y, z, 0, -1, 0)]) / 2.0;
-                grad[2 * L.n + s] = (h[L.shifted(x, y, z, 0, 0, 1)] - h[L.shifted(x, y, z, 0, 0, -1)]) / 2.0;
+                if (stencil == 0) {
+                    grad[0 * L.n + s] = (h[L.shifted(x, y, z, 1, 0, 0)] - h[L.shifted(x, y, z, -1, 0, 0)]) / 2.0;
+                    grad[1 * L.n + s] = (h[L.shifted(x, y, z, 0, 1, 0)] - h[L.shifted(x, y, z, 0, -1, 0)]) / 2.0;
+                    grad[2 * L.n + s] = (h[L.shifted(x, y, z, 0, 0, 1)] - h[L.shifted(x, y, z, 0, 0, -1)]) / 2.0;
+                } else {
+                    T g[3] = {T(0.0), T(0.0), T(0.0)};
+                    for (int i = 1; i < kQ; ++i) {
+                        const T hi = h[L.shifted(x, y, z, kCx[i], kCy[i], kCz[i])];
+                        const int c[3] = {kCx[i], kCy[i], kCz[i]};
+                        for (int a = 0; a < 3; ++a)
+                            if (c[a] > 0)
+                                g[a] += grad19_coef(i) * hi;
+                            else if (c[a] < 0)
+                                g[a] -= grad19_coef(i) * hi;
+                    }
+                    for (int a = 0; a < 3; ++a) grad[a * L.n + s] = g[a];
+                }
             }
 }
 
 // mu = A phi + B phi^3 - kappa lap(phi).
 template <class T>
 void chemical_potential(const Lattice& L, const Params<T>& p, const T* phi, T* lap, T* mu) {
-    laplacian(L, phi, lap);
+    laplacian(L, phi, lap, p.stencil);
 #pragma omp parallel for schedule(static)
     for (long s = 0; s < L.n; ++s)
         mu[s] = p.A * phi[s] + p.B * phi[s] * phi[s] * phi[s] - p.kappa * lap[s];
@@ -244,7 +280,7 @@ void macroscopic(const Lattice& L, const Params<T>& p, const T* f, const T* g, M
         m.phi[s] = phi;
     }
     chemical_potential(L, p, m.phi.data(), m.lap.data(), m.mu.data());
-    gradient(L, m.mu.data(), m.gradmu.data());
+    gradient(L, m.mu.data(), m.gradmu.data(), p.stencil);
 #pragma omp parallel for schedule(static)
     for (long s = 0; s < n; ++s)
         for (int a = 0; a < 3; ++a) {
@@ -314,8 +350,9 @@ void init_state(const Lattice& L, const Params<T>& p, const T* phi, const T* rho
     }
 }
 
+// prm = {A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil}; stencil 0 or 1.
 Params<double> params_from(const double* prm) {
-    return Params<double>{prm[0], prm[1], prm[2], prm[3], prm[4], prm[5], prm[6]};
+    return Params<double>{prm[0], prm[1], prm[2], prm[3], prm[4], prm[5], prm[6], prm[7] != 0.0 ? 1 : 0};
 }
 
 Params<Dual> dual_params_from(const double* prm, const double* dprm) {
@@ -327,6 +364,7 @@ Params<Dual> dual_params_from(const double* prm, const double* dprm) {
     p.tau_f = Dual(prm[4], dprm[4]);
     p.tau_g = Dual(prm[5], dprm[5]);
     p.rho0 = Dual(prm[6], dprm[6]);
+    p.stencil = prm[7] != 0.0 ? 1 : 0;  // not a differentiated parameter
     return p;
 }
 
@@ -350,11 +388,12 @@ double plane_ordered_sum(const Lattice& L, const double* a) {
 
 // ---------------------------------------------------------------------------
 // C interface (called from Python through ctypes by the tests only).
-// prm = {A, B, kappa, Gamma, tau_f, tau_g, rho0}. Return 0 on success, -1 on
-// bad arguments.
+// prm = {A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil}; the derivative
+// direction dprm has the first seven. Return 0 on success, -1 on bad
+// arguments.
 extern "C" {
 
-int orc_version() { return 1; }
+int orc_version() { return 2; }
 
 void orc_set_threads(int n) {
 #ifdef _OPENMP
@@ -391,15 +430,15 @@ void orc_guo(const double* u, const double* F, double tau, double* out) {
     guo_site(u, F, tau, out);
 }
 
-int orc_laplacian(int nx, int ny, int nz, const double* phi, double* lap) {
-    if (!dims_ok(nx, ny, nz) || !phi || !lap) return -1;
-    laplacian(Lattice(nx, ny, nz), phi, lap);
+int orc_laplacian(int nx, int ny, int nz, int stencil, const double* phi, double* lap) {
+    if (!dims_ok(nx, ny, nz) || !phi || !lap || (stencil != 0 && stencil != 1)) return -1;
+    laplacian(Lattice(nx, ny, nz), phi, lap, stencil);
     return 0;
 }
 
-int orc_gradient(int nx, int ny, int nz, const double* h, double* grad) {
-    if (!dims_ok(nx, ny, nz) || !h || !grad) return -1;
-    gradient(Lattice(nx, ny, nz), h, grad);
+int orc_gradient(int nx, int ny, int nz, int stencil, const double* h, double* grad) {
+    if (!dims_ok(nx, ny, nz) || !h || !grad || (stencil != 0 && stencil != 1)) return -1;
+    gradient(Lattice(nx, ny, nz), h, grad, stencil);
     return 0;
 }
 
@@ -445,7 +484,7 @@ int orc_macros(int nx, int ny, int nz, const double* prm, const double* f, const
     if (phi) std::memcpy(phi, m.phi.data(), sizeof(double) * n);
     if (mu) std::memcpy(mu, m.mu.data(), sizeof(double) * n);
     if (force) std::memcpy(force, m.F.data(), sizeof(double) * 3 * n);
-    if (gradphi) gradient(L, m.phi.data(), gradphi);
+    if (gradphi) gradient(L, m.phi.data(), gradphi, params_from(prm).stencil);
     if (totals) {
         totals[0] = plane_ordered_sum(L, m.rho.data());
         totals[1] = plane_ordered_sum(L, m.phi.data());

@@ -398,7 +398,7 @@ def test_tangent_linear_matches_finite_differences(orc):
     target = inputs.spinodal_phi(nx, ny, nz, seed=22, amplitude=0.3)
     rng = np.random.default_rng(5)
     dphi = rng.standard_normal(phi0.shape)
-    dprm = np.zeros(7)
+    dprm = np.zeros(8)  # the stencil entry is not differentiated
     dprm[2] = 0.3  # kappa
     dprm[4] = -0.7  # tau_f
     steps = 6
@@ -409,3 +409,136 @@ def test_tangent_linear_matches_finite_differences(orc):
     lm = orc.loss(phi0 - h * dphi, target, prm - h * dprm, steps)
     fd = (lp - lm) / (2 * h)
     assert dL == pytest.approx(fd, rel=1e-7)
+
+
+# --------------------------------------------------------------------------
+# 19-point isotropic stencils (catches weights swapped between axis and
+# diagonal neighbours, a missing or doubled neighbour, a sign error in the
+# gradient, an axis mix-up, and any form whose leading error is anisotropic).
+
+
+def _axis_field(shape, axis, seed):
+    """Random values along one axis, constant across the other two."""
+    rng = np.random.default_rng(seed)
+    line = rng.standard_normal(shape[axis])
+    view = [1, 1, 1]
+    view[axis] = shape[axis]
+    return np.broadcast_to(line.reshape(view), shape).copy()
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_isotropic_stencils_reduce_to_1d_forms(orc, axis):
+    """On a field that varies along one axis only, every diagonal neighbour
+    of the 19-point forms sees the same value as an axis neighbour, and the
+    sums collapse to the 1-D second difference and central difference: the
+    7-point results, to rounding."""
+    phi = _axis_field((6, 7, 8), axis, seed=axis)
+    assert np.abs(orc.laplacian(phi, 19) - orc.laplacian(phi, 7)).max() < 1e-14
+    assert np.abs(orc.gradient(phi, 19) - orc.gradient(phi, 7)).max() < 1e-14
+
+
+def test_isotropic_stencils_on_constants_and_sums(orc):
+    rng = np.random.default_rng(4)
+    phi = rng.standard_normal((5, 6, 7))
+    assert np.abs(orc.laplacian(np.full((5, 6, 7), 0.7), 19)).max() < 1e-15
+    assert np.abs(orc.gradient(np.full((5, 6, 7), 0.7), 19)).max() < 1e-15
+    # periodic sums of differences telescope
+    assert abs(orc.laplacian(phi, 19).sum()) < 1e-12
+    assert np.abs(orc.gradient(phi, 19).reshape(3, -1).sum(1)).max() < 1e-12
+
+
+def _modes(n):
+    z, y, x = np.meshgrid(np.arange(4), np.arange(n), np.arange(n), indexing="ij")
+    return x, y, z
+
+
+@pytest.mark.parametrize("m", [(5, 0, 0), (3, 4, 0), (0, 4, 3)])
+def test_isotropic_laplacian_symbol(orc, m):
+    """Both Laplacians have the discrete Fourier modes as eigenfunctions. For
+    the 19-point form, sum_i w_i c c c c is isotropic on D3Q19, so its symbol
+    is -|k|^2 + |k|^4/12 + O(k^6) in every direction; the 7-point symbol's k^4
+    term is sum_a k_a^4/12, which depends on the direction."""
+    n = 64
+    x, y, _ = _modes(n)
+    k = np.array(m[:2]) * 2 * math.pi / n if m[2] == 0 else None
+    if k is None:  # (0, 4, 3): along y and z needs nz = 64
+        z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(4), indexing="ij")
+        kv = np.array([0.0, 4.0, 3.0]) * 2 * math.pi / n
+        arg = kv[1] * y + kv[2] * z + 0.3
+    else:
+        kv = np.array([k[0], k[1], 0.0])
+        arg = kv[0] * x + kv[1] * y + 0.3
+    phi = np.cos(arg)
+    kk = float(kv @ kv)
+    s19 = float((orc.laplacian(phi, 19) * phi).sum() / (phi * phi).sum())
+    s7 = float((orc.laplacian(phi, 7) * phi).sum() / (phi * phi).sum())
+    assert abs(s19 - (-kk + kk * kk / 12)) < 1e-4
+    aniso7 = sum(ka ** 4 for ka in kv) / 12 - kk * kk / 12  # 7-point k^4 term minus the isotropic one
+    assert abs((s7 - s19) - aniso7) < 2e-4
+
+
+def test_isotropic_gradient_follows_k(orc):
+    """grad of sin(k.x) is G(k) cos(k.x). For the 19-point form G is k (1 -
+    |k|^2/6 + ...): parallel to k to O(k^5). The central difference gives
+    sin(k_a), whose direction departs from k at O(k^3)."""
+    n = 64
+    x, y, _ = _modes(n)
+    kv = np.array([3.0, 4.0, 0.0]) * 2 * math.pi / n
+    arg = kv[0] * x + kv[1] * y
+    h, cs = np.sin(arg), np.cos(arg)
+
+    def symbol(st):
+        gr = orc.gradient(h, st)
+        return np.array([(gr[a] * cs).sum() / (cs * cs).sum() for a in range(3)])
+
+    def angle(g):
+        return math.acos(min(1.0, float(g @ kv) / (np.linalg.norm(g) * np.linalg.norm(kv))))
+
+    g19, g7 = symbol(19), symbol(7)
+    kk = float(kv @ kv)
+    assert angle(g19) < 1e-4 < 1e-3 < angle(g7)
+    assert np.abs(g19 - kv * (1 - kk / 6)).max() < 1e-3
+    assert np.abs(g7 - np.sin(kv)).max() < 1e-14
+
+
+def test_isotropic_spinodal_growth_rate(orc):
+    """With the 19-point stencils a diagonal mode (k along (3, 4, 0)) grows at
+    omega = M lambda (-A - kappa lambda) with lambda = |k|^2 - |k|^4/12 (the
+    isotropic symbol above), at the same |k| = 2 pi / 32 as the axis-mode pin
+    above: the step uses the selected stencil in mu."""
+    const = golden_constants()
+    prm = orc.param_vector(stencil=19)
+    A, kappa = prm[0], prm[2]
+    n = 160
+    kv = np.array([3.0, 4.0]) * 2 * math.pi / n  # |k| = 5 (2 pi / 160) = 2 pi / 32
+    kk = float(kv @ kv)
+    lam = kk - kk * kk / 12
+    omega = const["M"] * lam * (-A - kappa * lam)
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    basis = np.cos(kv[0] * x + kv[1] * y)[None]
+    f, g = orc.init(1e-4 * basis, prm)
+    f, g = orc.step(f, g, prm, 200)
+    a0 = float((g.sum(0) * basis).sum())
+    f, g = orc.step(f, g, prm, 800)
+    a1 = float((g.sum(0) * basis).sum())
+    rate = math.log(a1 / a0) / 800
+    assert abs(rate / omega - 1.0) < 0.03
+
+
+@pytest.mark.parametrize("stencil", [7, 19])
+def test_step_uses_selected_stencils(orc, stencil):
+    """mu, the force and grad(phi) of the macroscopic output are built from
+    the stencil pair the parameters select (each pinned above): a step that
+    ignored the selection would fail one of the two cases."""
+    prm = orc.param_vector(stencil=stencil, kappa=0.07)
+    A, B, kappa = prm[0], prm[1], prm[2]
+    phi = inputs.spinodal_phi(9, 8, 7, seed=31, amplitude=0.4)
+    f, g = orc.init(phi, prm)
+    m = orc.macros(f, g, prm)
+    phi = m["phi"]  # sum of g, within rounding of the input
+    mu = A * phi + B * phi ** 3 - kappa * orc.laplacian(phi, stencil)
+    assert np.abs(m["mu"] - mu).max() < 1e-15
+    assert np.abs(m["force"] + phi * orc.gradient(m["mu"], stencil)).max() < 1e-16
+    assert np.abs(m["grad_phi"] - orc.gradient(phi, stencil)).max() < 1e-16
+    other = 19 if stencil == 7 else 7
+    assert np.abs(m["mu"] - (A * phi + B * phi ** 3 - kappa * orc.laplacian(phi, other))).max() > 1e-4
