@@ -65,6 +65,16 @@ enum { LD_FP64 = 0, LD_FP32 = 1, LD_FP16DEV = 2, LD_BF16DEV = 3 };
  * launches do less FP64 work per site (no halo phi sums). */
 enum { LD_KERNEL_AUTO = 0, LD_KERNEL_GENERIC = 1, LD_KERNEL_FUSED = 2, LD_KERNEL_FUSED_TMA = 3 };
 
+/* Stencils of the order-parameter gradients (mu's Laplacian, the force's
+ * gradient of mu, the grad phi output). The paper names these kernels
+ * ("Order Parameter Gradients", Sec. 2.1.1) without their forms.
+ * LD_STENCIL_7: 7-point Laplacian and 2-point central difference (default).
+ * LD_STENCIL_19: 19-point isotropic forms on the D3Q19 neighbourhood,
+ *   lap h = sum_i 6 w_i (h(x + c_i) - h(x)), grad h = sum_i 3 w_i c_i h(x + c_i),
+ *   whose leading truncation errors do not depend on direction; GENERIC and
+ *   FUSED kernels only (LD_EINVAL with LD_KERNEL_FUSED_TMA). */
+enum { LD_STENCIL_7 = 0, LD_STENCIL_19 = 1 };
+
 enum {
     LD_OK = 0,
     LD_EINVAL = -1,     /* bad argument: dims < 4, null/host pointer, tau <= 1/2, small workspace */
@@ -79,6 +89,7 @@ typedef struct {
     double rho0;               /* reference density (default rho, f deviation reference) */
     int precision;             /* LD_FP64 .. LD_BF16DEV */
     int kernel;                /* LD_KERNEL_AUTO / GENERIC / FUSED / FUSED_TMA */
+    int stencil;               /* LD_STENCIL_7 / LD_STENCIL_19 */
 } ld_params;
 
 typedef struct ld_ctx ld_ctx;

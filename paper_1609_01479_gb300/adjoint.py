@@ -37,6 +37,7 @@ class RunSpec:
     Gamma: float = 0.5
     tau_g: float = 1.0
     rho0: float = 1.0
+    stencil: int = 7  # 7-point Laplacian and central difference, or 19-point isotropic
 
 
 class LdRun(torch.autograd.Function):
@@ -48,7 +49,8 @@ class LdRun(torch.autograd.Function):
         if spec.steps < 0 or spec.checkpoint_every < 1:
             raise ValueError("steps must be >= 0 and checkpoint_every >= 1")
         sim = ld.LdSim(spec.nx, spec.ny, spec.nz, precision=spec.precision, kernel=spec.kernel, A=spec.A, B=spec.B,
-                       kappa=float(kappa), Gamma=spec.Gamma, tau_f=float(tau_f), tau_g=spec.tau_g, rho0=spec.rho0)
+                       kappa=float(kappa), Gamma=spec.Gamma, tau_f=float(tau_f), tau_g=spec.tau_g, rho0=spec.rho0,
+                       stencil=spec.stencil)
         phi0 = phi0.detach().to(device=sim.device, dtype=torch.float64).contiguous()
         sim.init(phi0)
         checkpoints = []

@@ -78,9 +78,17 @@ __global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<P>())
         const int zp = wrap_inc(z, g.nz), zm = wrap_dec(z, g.nz);
         // forward quantities
         const R ph = phi[s];
-        const R gmx = R(0.5) * (mu[site_of(g, xp, y, z)] - mu[site_of(g, xm, y, z)]);
-        const R gmy = R(0.5) * (mu[site_of(g, x, yp, z)] - mu[site_of(g, x, ym, z)]);
-        const R gmz = R(0.5) * (mu[site_of(g, x, y, zp)] - mu[site_of(g, x, y, zm)]);
+        R gmx, gmy, gmz;
+        if (m.iso) {
+            auto nb = [&](int i) {
+                return mu[site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny), step_coord(z, cz(i), g.nz))];
+            };
+            grad19(nb, gmx, gmy, gmz);
+        } else {
+            gmx = R(0.5) * (mu[site_of(g, xp, y, z)] - mu[site_of(g, xm, y, z)]);
+            gmy = R(0.5) * (mu[site_of(g, x, yp, z)] - mu[site_of(g, x, ym, z)]);
+            gmz = R(0.5) * (mu[site_of(g, x, y, zp)] - mu[site_of(g, x, y, zm)]);
+        }
         const R Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
         R f[Q];
         R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
@@ -161,26 +169,62 @@ __global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<P>())
     block_sum_one(omega_bar, part + 2 * (long long)blockIdx.x);
 }
 
-// Step 3: mubar += transposed central difference of gmbar; kappa partials.
+// Step 3: mubar += transpose of the gradient applied to gmbar; kappa
+// partials mubar (-lap phi). 7-point: the transposed central difference;
+// 19-point: mubar(y) += sum_i 3 w_i c_i . gmbar(y - c_i).
 template <class R>
 __global__ void __launch_bounds__(kAdjThreads)
-    k_adj_mu(Geom g, const R* __restrict__ phi, const R* __restrict__ gmb, R* __restrict__ mub,
+    k_adj_mu(Geom g, int iso, const R* __restrict__ phi, const R* __restrict__ gmb, R* __restrict__ mub,
              double* __restrict__ part) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double kappa_bar = 0.0;
     if (s < g.n) {
         int x, y, z;
         site_coords(g, s, x, y, z);
-        const long long sxm = site_of(g, wrap_dec(x, g.nx), y, z), sxp = site_of(g, wrap_inc(x, g.nx), y, z);
-        const long long sym = site_of(g, x, wrap_dec(y, g.ny), z), syp = site_of(g, x, wrap_inc(y, g.ny), z);
-        const long long szm = site_of(g, x, y, wrap_dec(z, g.nz)), szp = site_of(g, x, y, wrap_inc(z, g.nz));
-        const R t = mub[s] + R(0.5) * (gmb[sxm] - gmb[sxp]) + R(0.5) * (gmb[g.npad + sym] - gmb[g.npad + syp]) +
-                    R(0.5) * (gmb[2 * g.npad + szm] - gmb[2 * g.npad + szp]);
+        R t, lap;
+        if (iso) {
+            t = mub[s];
+            lap = R(0);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const long long back = site_of(g, step_coord(x, -cx(i), g.nx), step_coord(y, -cy(i), g.ny),
+                                               step_coord(z, -cz(i), g.nz));
+                const long long fwd = site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny),
+                                              step_coord(z, cz(i), g.nz));
+                const R dot = cdot(i, gmb[back], gmb[g.npad + back], gmb[2 * g.npad + back]);
+                t += grad19_coef<R>(i) * dot;
+                lap += lap19_coef<R>(i) * (phi[fwd] - phi[s]);
+            }
+        } else {
+            const long long sxm = site_of(g, wrap_dec(x, g.nx), y, z), sxp = site_of(g, wrap_inc(x, g.nx), y, z);
+            const long long sym = site_of(g, x, wrap_dec(y, g.ny), z), syp = site_of(g, x, wrap_inc(y, g.ny), z);
+            const long long szm = site_of(g, x, y, wrap_dec(z, g.nz)), szp = site_of(g, x, y, wrap_inc(z, g.nz));
+            t = mub[s] + R(0.5) * (gmb[sxm] - gmb[sxp]) + R(0.5) * (gmb[g.npad + sym] - gmb[g.npad + syp]) +
+                R(0.5) * (gmb[2 * g.npad + szm] - gmb[2 * g.npad + szp]);
+            lap = phi[sxp] + phi[sxm] + phi[syp] + phi[sym] + phi[szp] + phi[szm] - R(6) * phi[s];
+        }
         mub[s] = t;
-        const R lap = phi[sxp] + phi[sxm] + phi[syp] + phi[sym] + phi[szp] + phi[szm] - R(6) * phi[s];
         kappa_bar = -(double)t * (double)lap;
     }
     block_sum_one(kappa_bar, part + 2 * (long long)blockIdx.x + 1);
+}
+
+// Laplacian (7-point or 19-point, symmetric: its own transpose) of a field
+// at site s = (x, y, z), in the type of the field.
+template <class T>
+__device__ __forceinline__ T lap_at(const Geom& g, int iso, const T* h, long long s, int x, int y, int z) {
+    if (iso) {
+        T lap = T(0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i)
+            lap += lap19_coef<T>(i) *
+                   (h[site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny), step_coord(z, cz(i), g.nz))] -
+                    h[s]);
+        return lap;
+    }
+    return h[site_of(g, wrap_inc(x, g.nx), y, z)] + h[site_of(g, wrap_dec(x, g.nx), y, z)] +
+           h[site_of(g, x, wrap_inc(y, g.ny), z)] + h[site_of(g, x, wrap_dec(y, g.ny), z)] +
+           h[site_of(g, x, y, wrap_inc(z, g.nz))] + h[site_of(g, x, y, wrap_dec(z, g.nz))] - T(6) * h[s];
 }
 
 // Step 4: phibar, the per-site part P of gbar at t.
@@ -193,9 +237,7 @@ __global__ void __launch_bounds__(kAdjThreads)
     int x, y, z;
     site_coords(g, s, x, y, z);
     const R ph = phi[s];
-    const R lapm = mub[site_of(g, wrap_inc(x, g.nx), y, z)] + mub[site_of(g, wrap_dec(x, g.nx), y, z)] +
-                   mub[site_of(g, x, wrap_inc(y, g.ny), z)] + mub[site_of(g, x, wrap_dec(y, g.ny), z)] +
-                   mub[site_of(g, x, y, wrap_inc(z, g.nz))] + mub[site_of(g, x, y, wrap_dec(z, g.nz))] - R(6) * mub[s];
+    const R lapm = lap_at(g, m.iso, mub, s, x, y, z);
     pb0[s] = phib[s] + (m.A + R(3) * m.B * ph * ph) * mub[s] - m.kappa * lapm;
 }
 
@@ -272,9 +314,6 @@ __global__ void __launch_bounds__(kAdjThreads)
     if (s < g.n) {
         int x, y, z;
         site_coords(g, s, x, y, z);
-        const long long sxp = site_of(g, wrap_inc(x, g.nx), y, z), sxm = site_of(g, wrap_dec(x, g.nx), y, z);
-        const long long syp = site_of(g, x, wrap_inc(y, g.ny), z), sym = site_of(g, x, wrap_dec(y, g.ny), z);
-        const long long szp = site_of(g, x, y, wrap_inc(z, g.nz)), szm = site_of(g, x, y, wrap_dec(z, g.nz));
         R ux = R(0), uy = R(0), uz = R(0);
         if (u0) {
             ux = (R)u0[s];
@@ -292,9 +331,9 @@ __global__ void __launch_bounds__(kAdjThreads)
         }
         const R ph = (R)phi0[s];
         const R mb = mub[s];
-        const R lapm = mub[sxp] + mub[sxm] + mub[syp] + mub[sym] + mub[szp] + mub[szm] - R(6) * mb;
+        const R lapm = lap_at(g, m.iso, mub, s, x, y, z);
         grad_phi0[s] = (double)(acc + (m.A + R(3) * m.B * ph * ph) * mb - m.kappa * lapm);
-        const double lap = phi0[sxp] + phi0[sxm] + phi0[syp] + phi0[sym] + phi0[szp] + phi0[szm] - 6.0 * phi0[s];
+        const double lap = lap_at(g, m.iso, phi0, s, x, y, z);
         kappa_bar = -(double)mb * lap;
     }
     if (threadIdx.x == 0) part[2 * (long long)blockIdx.x] = 0.0;  // no tau_f term in the initialiser
@@ -361,7 +400,7 @@ cudaError_t adj_step_p(ld_ctx* c, const void* state_t, const void* fields_t, dou
     const unsigned nb = blocks_for(g.n);
     k_adj_local<P><<<nb, kAdjThreads, 0, c->stream>>>(g, m, (const S*)f_part(c, state_t), phi, mu, c->ref, p.fb1,
                                                       p.gb1, p.pb1, p.fb0, p.gb0, p.gmb, p.mub, p.phib, c->adj_part);
-    k_adj_mu<R><<<nb, kAdjThreads, 0, c->stream>>>(g, phi, p.gmb, p.mub, c->adj_part);
+    k_adj_mu<R><<<nb, kAdjThreads, 0, c->stream>>>(g, m.iso, phi, p.gmb, p.mub, c->adj_part);
     k_adj_p<R><<<nb, kAdjThreads, 0, c->stream>>>(g, m, phi, p.mub, p.phib, p.pb0);
     if (grad)
         k_adj_finalize<<<1, kAdjThreads, 0, c->stream>>>(c->adj_part, nb, -1.0 / (c->prm.tau_f * c->prm.tau_f),

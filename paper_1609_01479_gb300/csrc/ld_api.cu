@@ -81,6 +81,9 @@ bool params_ok(const ld_params* p, const char** why) {
         return *why = "A, B, kappa, Gamma must be finite", false;
     if (p->precision < LD_FP64 || p->precision > LD_BF16DEV) return *why = "unknown precision", false;
     if (p->kernel < LD_KERNEL_AUTO || p->kernel > LD_KERNEL_FUSED_TMA) return *why = "unknown kernel", false;
+    if (p->stencil != LD_STENCIL_7 && p->stencil != LD_STENCIL_19) return *why = "unknown stencil", false;
+    if (p->stencil == LD_STENCIL_19 && p->kernel == LD_KERNEL_FUSED_TMA)
+        return *why = "the TMA-staged kernel has the 7-point stencils only", false;
     return true;
 }
 

@@ -91,6 +91,7 @@ struct Model {
     R A, B, kappa, Gamma;
     R omega_f, omega_g;  // 1/tau
     R force_pre;         // 1 - 1/(2 tau_f)
+    int iso;             // 1: 19-point isotropic stencils (LD_STENCIL_19)
 };
 
 // Model constants from the C-ABI parameters.
@@ -104,6 +105,7 @@ inline Model<R> model_of(const ld_params& p) {
     m.omega_f = (R)(1.0 / p.tau_f);
     m.omega_g = (R)(1.0 / p.tau_g);
     m.force_pre = (R)(1.0 - 0.5 / p.tau_f);
+    m.iso = p.stencil == LD_STENCIL_19 ? 1 : 0;
     return m;
 }
 
@@ -125,13 +127,53 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 
-// mu = A phi + B phi^3 - kappa lap, with lap = (sum of the six neighbours'
-// phi) - 6 phi; operations in that order, each rounded once.
+// mu = A phi + B phi^3 - kappa lap; operations in that order, each rounded once.
 template <class R>
-__device__ __forceinline__ R chem_potential(R phi, R nb_sum, const Model<R>& m) {
-    const R lap = sub_rn(nb_sum, mul_rn(R(6), phi));
+__device__ __forceinline__ R chem_potential_lap(R phi, R lap, const Model<R>& m) {
     const R cubic = mul_rn(mul_rn(mul_rn(m.B, phi), phi), phi);
     return sub_rn(add_rn(mul_rn(m.A, phi), cubic), mul_rn(m.kappa, lap));
+}
+
+// The same with the 7-point lap = (sum of the six axis neighbours' phi) - 6 phi.
+template <class R>
+__device__ __forceinline__ R chem_potential(R phi, R nb_sum, const Model<R>& m) {
+    return chem_potential_lap(phi, sub_rn(nb_sum, mul_rn(R(6), phi)), m);
+}
+
+// 19-point isotropic forms on the D3Q19 neighbourhood. nb(i) is h(x + c_i).
+//   lap h  = sum_{i=1..18} 6 w_i (h(x + c_i) - h(x)),  6 w_i = 1/3 (axis), 1/6 (diagonal)
+//   grad h = sum_{i=1..18} 3 w_i c_i h(x + c_i),       3 w_i = 1/6 (axis), 1/12 (diagonal)
+// Summed in velocity order with every operation rounded once, so that each
+// kernel that forms them gets the same bits (and FP64 follows the plain
+// operation order); components with c_ia = 0 contribute nothing.
+template <class R>
+__device__ __forceinline__ R lap19_coef(int i) {
+    return i <= 6 ? R(1) / R(3) : R(1) / R(6);
+}
+template <class R>
+__device__ __forceinline__ R grad19_coef(int i) {
+    return i <= 6 ? R(1) / R(6) : R(1) / R(12);
+}
+template <class R, class F>
+__device__ __forceinline__ R lap19(R h0, F nb) {
+    R sum = R(0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) sum = add_rn(sum, mul_rn(lap19_coef<R>(i), sub_rn(nb(i), h0)));
+    return sum;
+}
+template <class R, class F>
+__device__ __forceinline__ void grad19(F nb, R& gx, R& gy, R& gz) {
+    gx = gy = gz = R(0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const R t = mul_rn(grad19_coef<R>(i), nb(i));
+        if (cx(i) > 0) gx = add_rn(gx, t);
+        if (cx(i) < 0) gx = sub_rn(gx, t);
+        if (cy(i) > 0) gy = add_rn(gy, t);
+        if (cy(i) < 0) gy = sub_rn(gy, t);
+        if (cz(i) > 0) gz = add_rn(gz, t);
+        if (cz(i) < 0) gz = sub_rn(gz, t);
+    }
 }
 
 // c_i . (ax, ay, az) over the nonzero components of c_i only, in x, y, z

@@ -46,7 +46,9 @@ __device__ __forceinline__ int wrap_once(int a, int n) { return a < 0 ? a + n : 
 // I: type of the element offsets i * npad + s. A 32-bit offset keeps the
 // 19 per-direction offsets, which the compiler holds for the whole kernel,
 // in one register each; 64-bit only where 19 npad does not fit in it.
-template <int P, int TY, class I>
+// ISO: the 19-point isotropic stencils (mu's Laplacian over the phi ring,
+// grad mu over the mu ring, corners included) instead of the 7-point ones.
+template <int P, int TY, class I, bool ISO>
 __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     k_step_fused(Geom g, Model<typename Prec<P>::real_t> m, int zc,
                  const typename Prec<P>::store_t* __restrict__ fs, const typename Prec<P>::store_t* __restrict__ gs,
@@ -102,9 +104,14 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
         for (int idx = tid; idx < MW * MH; idx += NT) {
             const int mx = idx % MW, my = idx / MW;
             const int hx = mx + 1, hy = my + 1;
-            const R nb = phis[mid][hy][hx + 1] + phis[mid][hy][hx - 1] + phis[mid][hy + 1][hx]
-                       + phis[mid][hy - 1][hx] + phis[hi][hy][hx] + phis[lo][hy][hx];
-            mus[slot][my][mx] = chem_potential(phis[mid][hy][hx], nb, m);
+            if constexpr (ISO) {
+                auto nb = [&](int i) { return phis[cz(i) > 0 ? hi : (cz(i) < 0 ? lo : mid)][hy + cy(i)][hx + cx(i)]; };
+                mus[slot][my][mx] = chem_potential_lap(phis[mid][hy][hx], lap19(phis[mid][hy][hx], nb), m);
+            } else {
+                const R nb = phis[mid][hy][hx + 1] + phis[mid][hy][hx - 1] + phis[mid][hy + 1][hx]
+                           + phis[mid][hy - 1][hx] + phis[hi][hy][hx] + phis[lo][hy][hx];
+                mus[slot][my][mx] = chem_potential(phis[mid][hy][hx], nb, m);
+            }
         }
     };
     auto ps = [&](int zp) { return (zp - z0 + 2) % 3; };  // phi slot of plane zp (zp >= z0-2)
@@ -152,9 +159,16 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
         const R ph = phis[ps(k)][ty + 2][tx + 2];
         const int mc = ms(k);
         const R muc = mus[mc][ty + 1][tx + 1];
-        const R gmx = R(0.5) * (mus[mc][ty + 1][tx + 2] - mus[mc][ty + 1][tx]);
-        const R gmy = R(0.5) * (mus[mc][ty + 2][tx + 1] - mus[mc][ty][tx + 1]);
-        const R gmz = R(0.5) * (mus[ms(k + 1)][ty + 1][tx + 1] - mus[ms(k - 1)][ty + 1][tx + 1]);
+        R gmx, gmy, gmz;
+        if constexpr (ISO) {
+            const int mp = ms(k + 1), mm = ms(k - 1);
+            auto nb = [&](int i) { return mus[cz(i) > 0 ? mp : (cz(i) < 0 ? mm : mc)][ty + 1 + cy(i)][tx + 1 + cx(i)]; };
+            grad19(nb, gmx, gmy, gmz);
+        } else {
+            gmx = R(0.5) * (mus[mc][ty + 1][tx + 2] - mus[mc][ty + 1][tx]);
+            gmy = R(0.5) * (mus[mc][ty + 2][tx + 1] - mus[mc][ty][tx + 1]);
+            gmz = R(0.5) * (mus[ms(k + 1)][ty + 1][tx + 1] - mus[ms(k - 1)][ty + 1][tx + 1]);
+        }
         const R Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
         if (phi_out) {  // fields of the source state, for the adjoint
             phi_out[s] = ph;
@@ -220,14 +234,14 @@ int choose_zc(int nx, int ny, int nz, int num_sms = 152, int per_sm = 2) {
     return best;
 }
 
-template <int P, class I>
+template <int P, class I, bool ISO>
 cudaError_t launch_fused(ld_ctx* c, const void* src, void* dst, void* fields) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     constexpr size_t kRingBytes = sizeof(S) == 2 ? 3 * (size_t)Q * kTY * kTX * sizeof(S) : 0;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_fused<P, kTY, I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_step_fused<P, kTY, I, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kRingBytes);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -235,7 +249,7 @@ cudaError_t launch_fused(ld_ctx* c, const void* src, void* dst, void* fields) {
     const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
     const int zc = choose_zc(g.nx, g.ny, g.nz, c->num_sms, fused_ctas_per_sm<P>());
     const dim3 grid(g.nx / kTX, g.ny / kTY, g.nz / zc);
-    k_step_fused<P, kTY, I><<<grid, kTX * kTY, kRingBytes, c->stream>>>(
+    k_step_fused<P, kTY, I, ISO><<<grid, kTX * kTY, kRingBytes, c->stream>>>(
         g, model_of<R>(c->prm), zc, (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
         (S*)g_part(c, dst), c->ref, fields ? (R*)fields : nullptr, fields ? (R*)fields + c->geom.npad : nullptr);
     return cudaGetLastError();
@@ -243,8 +257,10 @@ cudaError_t launch_fused(ld_ctx* c, const void* src, void* dst, void* fields) {
 
 template <int P>
 cudaError_t step_fused_p(ld_ctx* c, const void* src, void* dst, void* fields) {
-    return (long long)Q * c->geom.npad <= 0x7fffffffLL ? launch_fused<P, int>(c, src, dst, fields)
-                                                        : launch_fused<P, long long>(c, src, dst, fields);
+    const bool small = (long long)Q * c->geom.npad <= 0x7fffffffLL;
+    if (c->prm.stencil == LD_STENCIL_19)
+        return small ? launch_fused<P, int, true>(c, src, dst, fields) : launch_fused<P, long long, true>(c, src, dst, fields);
+    return small ? launch_fused<P, int, false>(c, src, dst, fields) : launch_fused<P, long long, false>(c, src, dst, fields);
 }
 
 }  // namespace

@@ -84,6 +84,14 @@ __global__ void __launch_bounds__(kRowThreads) k_mu(RowGeom rg, Model<R> m, cons
     const int xp = x + 1 == nx ? 1 - nx : 1, xm = x == 0 ? nx - 1 : -1;
     const int yp = y + 1 == rg.ny ? (1 - rg.ny) * nx : nx, ym = y == 0 ? (rg.ny - 1) * nx : -nx;
     const int zp = z + 1 == rg.nz ? (1 - rg.nz) * plane : plane, zm = z == 0 ? (rg.nz - 1) * plane : -plane;
+    if (m.iso) {
+        auto nb = [&](int i) {
+            return phi[s + (cx(i) > 0 ? xp : (cx(i) < 0 ? xm : 0)) + (cy(i) > 0 ? yp : (cy(i) < 0 ? ym : 0)) +
+                       (cz(i) > 0 ? zp : (cz(i) < 0 ? zm : 0))];
+        };
+        mu[s] = chem_potential_lap(phi[s], lap19(phi[s], nb), m);
+        return;
+    }
     const R nb = phi[s + xp] + phi[s + xm] + phi[s + yp] + phi[s + ym] + phi[s + zp] + phi[s + zm];
     mu[s] = chem_potential(phi[s], nb, m);
 }
@@ -125,9 +133,18 @@ __global__ void __launch_bounds__(kRowThreads, rows_blocks_per_sm<P>())
     const int ozp = z + 1 == rg.nz ? (1 - rg.nz) * plane : plane, ozm = z == 0 ? (rg.nz - 1) * plane : -plane;
 
     const R ph = phi[s], muc = mu[s];
-    const R gmx = R(0.5) * (mu[s + oxp] - mu[s + oxm]);
-    const R gmy = R(0.5) * (mu[s + oyp] - mu[s + oym]);
-    const R gmz = R(0.5) * (mu[s + ozp] - mu[s + ozm]);
+    R gmx, gmy, gmz;
+    if (m.iso) {
+        auto nb = [&](int i) {
+            return mu[s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
+                      (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0))];
+        };
+        grad19(nb, gmx, gmy, gmz);
+    } else {
+        gmx = R(0.5) * (mu[s + oxp] - mu[s + oxm]);
+        gmy = R(0.5) * (mu[s + oyp] - mu[s + oym]);
+        gmz = R(0.5) * (mu[s + ozp] - mu[s + ozm]);
+    }
     const R Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
 
     R f[Q];
@@ -173,10 +190,19 @@ __global__ void __launch_bounds__(kThreads)
     int x, y, z;
     site_coords(g, s, x, y, z);
     const R p = (R)phi[s];
-    const R lap = (R)phi[site_of(g, wrap_inc(x, g.nx), y, z)] + (R)phi[site_of(g, wrap_dec(x, g.nx), y, z)]
-                + (R)phi[site_of(g, x, wrap_inc(y, g.ny), z)] + (R)phi[site_of(g, x, wrap_dec(y, g.ny), z)]
-                + (R)phi[site_of(g, x, y, wrap_inc(z, g.nz))] + (R)phi[site_of(g, x, y, wrap_dec(z, g.nz))]
-                - R(6) * p;
+    R lap;
+    if (m.iso) {
+        lap = R(0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i)
+            lap += lap19_coef<R>(i) *
+                   ((R)phi[site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny), step_coord(z, cz(i), g.nz))] -
+                    p);
+    } else {
+        lap = (R)phi[site_of(g, wrap_inc(x, g.nx), y, z)] + (R)phi[site_of(g, wrap_dec(x, g.nx), y, z)]
+            + (R)phi[site_of(g, x, wrap_inc(y, g.ny), z)] + (R)phi[site_of(g, x, wrap_dec(y, g.ny), z)]
+            + (R)phi[site_of(g, x, y, wrap_inc(z, g.nz))] + (R)phi[site_of(g, x, y, wrap_dec(z, g.nz))] - R(6) * p;
+    }
     const R mu = m.A * p + m.B * p * p * p - m.kappa * lap;
     const R rho = (R)(rho_in ? rho_in[s] : rho0);
     R ux = R(0), uy = R(0), uz = R(0);
@@ -304,7 +330,7 @@ __global__ void __launch_bounds__(kThreads)
              const typename Prec<P>::store_t* __restrict__ gs, const typename Prec<P>::real_t* __restrict__ phis,
              const typename Prec<P>::real_t* __restrict__ mu, const float* __restrict__ ref,
              double* __restrict__ rho_out, double* __restrict__ u_out, double* __restrict__ phi_out,
-             double* __restrict__ gphi_out) {
+             double* __restrict__ gphi_out, int iso) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.n) return;
     int x, y, z;
@@ -324,19 +350,29 @@ __global__ void __launch_bounds__(kThreads)
     }
     if (rho_out) rho_out[s] = rho;
     if (phi_out) phi_out[s] = ph;
+    // gradient of a field (the selected stencil), in FP64
+    auto grad = [&](const typename Prec<P>::real_t* h, double& gx, double& gy, double& gz) {
+        if (iso) {
+            auto nb = [&](int i) {
+                return (double)h[site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny),
+                                         step_coord(z, cz(i), g.nz))];
+            };
+            grad19(nb, gx, gy, gz);
+        } else {
+            gx = 0.5 * ((double)h[site_of(g, xp, y, z)] - (double)h[site_of(g, xm, y, z)]);
+            gy = 0.5 * ((double)h[site_of(g, x, yp, z)] - (double)h[site_of(g, x, ym, z)]);
+            gz = 0.5 * ((double)h[site_of(g, x, y, zp)] - (double)h[site_of(g, x, y, zm)]);
+        }
+    };
     if (u_out) {
-        const double Fx = -ph * 0.5 * ((double)mu[site_of(g, xp, y, z)] - (double)mu[site_of(g, xm, y, z)]);
-        const double Fy = -ph * 0.5 * ((double)mu[site_of(g, x, yp, z)] - (double)mu[site_of(g, x, ym, z)]);
-        const double Fz = -ph * 0.5 * ((double)mu[site_of(g, x, y, zp)] - (double)mu[site_of(g, x, y, zm)]);
+        double gx, gy, gz;
+        grad(mu, gx, gy, gz);
+        const double Fx = -ph * gx, Fy = -ph * gy, Fz = -ph * gz;
         u_out[s] = (jx + 0.5 * Fx) / rho;
         u_out[g.n + s] = (jy + 0.5 * Fy) / rho;
         u_out[2 * g.n + s] = (jz + 0.5 * Fz) / rho;
     }
-    if (gphi_out) {
-        gphi_out[s] = 0.5 * ((double)phis[site_of(g, xp, y, z)] - (double)phis[site_of(g, xm, y, z)]);
-        gphi_out[g.n + s] = 0.5 * ((double)phis[site_of(g, x, yp, z)] - (double)phis[site_of(g, x, ym, z)]);
-        gphi_out[2 * g.n + s] = 0.5 * ((double)phis[site_of(g, x, y, zp)] - (double)phis[site_of(g, x, y, zm)]);
-    }
+    if (gphi_out) grad(phis, gphi_out[s], gphi_out[g.n + s], gphi_out[2 * g.n + s]);
 }
 
 // Distributions out (decoded, stride n) and in (encoded).
@@ -449,7 +485,7 @@ cudaError_t macros_p(ld_ctx* c, double* rho, double* u, double* phi, double* gph
     if (e != cudaSuccess) return e;
     k_macros<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, (const S*)f_of(c, c->cur), (const S*)g_of(c, c->cur),
                                                              (const R*)c->phi, (const R*)c->mu, c->ref, rho, u,
-                                                             phi, gphi);
+                                                             phi, gphi, c->prm.stencil == LD_STENCIL_19);
     return cudaGetLastError();
 }
 

@@ -27,13 +27,16 @@ PRECISIONS = {"fp64": LD_FP64, "fp32": LD_FP32, "fp16dev": LD_FP16DEV, "bf16dev"
 KERNELS = {"auto": LD_KERNEL_AUTO, "generic": LD_KERNEL_GENERIC, "fused": LD_KERNEL_FUSED,
            "fused_tma": LD_KERNEL_FUSED_TMA}
 STORE_BYTES = {LD_FP64: 8, LD_FP32: 4, LD_FP16DEV: 2, LD_BF16DEV: 2}
+LD_STENCIL_7, LD_STENCIL_19 = 0, 1
+STENCILS = {7: LD_STENCIL_7, 19: LD_STENCIL_19}
 Q = 19
 
 
 class LdParams(ctypes.Structure):
     _fields_ = [("A", ctypes.c_double), ("B", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("Gamma", ctypes.c_double), ("tau_f", ctypes.c_double), ("tau_g", ctypes.c_double),
-                ("rho0", ctypes.c_double), ("precision", ctypes.c_int), ("kernel", ctypes.c_int)]
+                ("rho0", ctypes.c_double), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("stencil", ctypes.c_int)]
 
 
 class LdError(RuntimeError):
@@ -116,10 +119,12 @@ def _call(name, ctx, *args):
 
 
 def make_params(A=-0.0625, B=0.0625, kappa=0.04, Gamma=0.5, tau_f=1.0, tau_g=1.0, rho0=1.0,
-                precision="fp32", kernel="auto") -> LdParams:
+                precision="fp32", kernel="auto", stencil=7) -> LdParams:
+    """ld_params; stencil is 7 (7-point Laplacian, central difference) or 19
+    (the 19-point isotropic forms)."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     kern = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-    return LdParams(A, B, kappa, Gamma, tau_f, tau_g, rho0, prec, kern)
+    return LdParams(A, B, kappa, Gamma, tau_f, tau_g, rho0, prec, kern, STENCILS[int(stencil)])
 
 
 # ---------------------------------------------------------------------------
@@ -282,6 +287,8 @@ class LdSim:
     def set_params(self, **model):
         p = self.params
         kw = {f[0]: getattr(p, f[0]) for f in LdParams._fields_}
+        if "stencil" in model:
+            model = dict(model, stencil=STENCILS[int(model["stencil"])])
         kw.update(model)
         self.params = LdParams(*[kw[f[0]] for f in LdParams._fields_])
         ld_set_params(self.ctx, self.params)

@@ -41,27 +41,28 @@ def gpu_grads(adjoint, phi0, target, kappa, tau_f, spec):
     return float(loss.item()), p0.grad.cpu().numpy(), float(k.grad.item()), float(t.grad.item())
 
 
-def oracle_prm(kappa, tau_f, tau_g=1.0):
-    return oracle.param_vector(kappa=kappa, tau_f=tau_f, tau_g=tau_g)
+def oracle_prm(kappa, tau_f, tau_g=1.0, stencil=7):
+    return oracle.param_vector(kappa=kappa, tau_f=tau_f, tau_g=tau_g, stencil=stencil)
 
 
-def target_phi(phi0, kappa_t, tau_f, steps):
-    prm = oracle_prm(kappa_t, tau_f)
+def target_phi(phi0, kappa_t, tau_f, steps, stencil=7):
+    prm = oracle_prm(kappa_t, tau_f, stencil=stencil)
     f, g = oracle.init(phi0, prm)
     f, g = oracle.step(f, g, prm, steps)
     return g.sum(axis=0)
 
 
+@pytest.mark.parametrize("stencil", [7, 19])
 @pytest.mark.parametrize("shape,steps,K,kernel", [((5, 6, 7), 12, 5, "generic"), ((4, 8, 32), 9, 4, "fused")])
-def test_dot_product_fp64(mods, shape, steps, K, kernel):
+def test_dot_product_fp64(mods, shape, steps, K, kernel, stencil):
     ld, adjoint = mods
     nz, ny, nx = shape
     phi0 = inputs.spinodal_phi(nx, ny, nz, seed=41, amplitude=0.3)
-    target = target_phi(phi0, 0.05, 0.9, steps)
+    target = target_phi(phi0, 0.05, 0.9, steps, stencil=stencil)
     kappa, tau_f = 0.04, 0.9
-    spec = adjoint.RunSpec(nx, ny, nz, steps, checkpoint_every=K, precision="fp64", kernel=kernel)
+    spec = adjoint.RunSpec(nx, ny, nz, steps, checkpoint_every=K, precision="fp64", kernel=kernel, stencil=stencil)
     L, gphi, gk, gt = gpu_grads(adjoint, phi0, target, kappa, tau_f, spec)
-    prm = oracle_prm(kappa, tau_f)
+    prm = oracle_prm(kappa, tau_f, stencil=stencil)
     assert L == pytest.approx(oracle.loss(phi0, target, prm, steps), rel=1e-11)
     rng = np.random.default_rng(7)
     for _ in range(3):

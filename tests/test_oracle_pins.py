@@ -391,9 +391,10 @@ def test_flat_interface_bulk_and_width(orc, B):
 # double path (catches a wrong derivative rule in the dual numbers).
 
 
-def test_tangent_linear_matches_finite_differences(orc):
+@pytest.mark.parametrize("stencil", [7, 19])
+def test_tangent_linear_matches_finite_differences(orc, stencil):
     nz, ny, nx = 5, 6, 4
-    prm = orc.param_vector(tau_f=0.9)
+    prm = orc.param_vector(tau_f=0.9, stencil=stencil)
     phi0 = inputs.spinodal_phi(nx, ny, nz, seed=21, amplitude=0.3)
     target = inputs.spinodal_phi(nx, ny, nz, seed=22, amplitude=0.3)
     rng = np.random.default_rng(5)

@@ -38,6 +38,8 @@ def rel_l2(a, b):
 def gpu_run(ld, phi, steps, precision="fp64", kernel="auto", prm=None, rho=None, u=None):
     nz, ny, nx = phi.shape
     model = {} if prm is None else dict(zip(oracle.PARAM_NAMES, map(float, prm)))
+    if "stencil" in model:  # the oracle's 0/1 selector -> the library's 7/19
+        model["stencil"] = 19 if model["stencil"] else 7
     sim = ld.LdSim(nx, ny, nz, precision=precision, kernel=kernel, **model)
     sim.init(torch.from_numpy(phi).cuda(),
              None if rho is None else torch.from_numpy(rho).cuda(),
@@ -110,6 +112,41 @@ def test_fp64_fused(ld, shape):
     phi = inputs.spinodal_phi(nx, ny, nz, seed=3, amplitude=0.3)
     prm = oracle.param_vector(tau_f=0.9, tau_g=1.1)
     assert_parity(gpu_run(ld, phi, 20, kernel="fused", prm=prm), oracle_run(phi, 20, prm=prm), FP64_TOL)
+
+
+@pytest.mark.parametrize("kernel,shape", [("generic", (7, 6, 5)), ("generic", (5, 9, 33)),
+                                          ("fused", (4, 8, 32)), ("fused", (12, 24, 32))])
+def test_fp64_isotropic_stencils(ld, kernel, shape):
+    """The 19-point isotropic Laplacian and gradient (LD_STENCIL_19): the
+    same 1e-12 bar against the oracle, on ragged lattices (generic) and tiled
+    ones whose rings wrap (fused; nz = 4 and ny = 8 make every diagonal
+    neighbour a periodic image)."""
+    nz, ny, nx = shape
+    phi = inputs.spinodal_phi(nx, ny, nz, seed=17, amplitude=0.3)
+    prm = oracle.param_vector(tau_f=0.9, tau_g=1.1, stencil=19)
+    assert_parity(gpu_run(ld, phi, 20, kernel=kernel, prm=prm), oracle_run(phi, 20, prm=prm), FP64_TOL)
+
+
+@pytest.mark.parametrize("kernel", ["generic", "fused"])
+def test_fp32_isotropic_stencils(ld, kernel):
+    """FP32 storage with the 19-point stencils: phi within the FP32 bound of
+    the oracle run with the same stencils, and measurably different from the
+    7-point run (the selection reaches the kernels)."""
+    nz, ny, nx = 32, 32, 32
+    phi = inputs.spinodal_phi(nx, ny, nz, seed=2)
+    prm = oracle.param_vector(stencil=19)
+    g = gpu_run(ld, phi, 100, precision="fp32", kernel=kernel, prm=prm)
+    r = oracle_run(phi, 100, prm=prm)
+    assert rel_l2(g["phi"], r["phi"]) <= 1e-5
+    assert rel_l2(g["grad_phi"], r["grad_phi"]) <= 1e-4
+    r7 = oracle_run(phi, 100)
+    assert rel_l2(r7["phi"], r["phi"]) > 1e-4
+
+
+def test_isotropic_stencils_refused_by_the_tma_kernel(ld):
+    with pytest.raises(ld.LdError) as e:
+        ld.LdSim(32, 8, 4, precision="fp32", kernel="fused_tma", stencil=19)
+    assert e.value.code == ld.LD_EINVAL
 
 
 def test_fp64_fused_with_flow_and_density(ld):
