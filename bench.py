@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--stencil", type=int, default=7, choices=[7, 19],
+                    help="order-parameter stencils: 7-point (default) or 19-point isotropic")
     return ap.parse_args()
 
 
@@ -61,7 +63,8 @@ def config_of(args):
     n = args.size
     return {"workload": f"spinodal-{n}^3-periodic", "lattice": [n, n, n], "sites": n ** 3,
             "init": "phi uniform seeded noise in [-0.05,0.05] (SplitMix64 seed 5), rho=1, u=0, f,g at equilibrium",
-            "params": {"A": -0.0625, "B": 0.0625, "kappa": 0.04, "Gamma": 0.5, "tau_f": 1.0, "tau_g": 1.0},
+            "params": {"A": -0.0625, "B": 0.0625, "kappa": 0.04, "Gamma": 0.5, "tau_f": 1.0, "tau_g": 1.0,
+                       "stencil": args.stencil},
             "bytes_per_site_algorithmic": None, "l2": "no flush: state is larger than L2 (129 MB)",
             "parallelism": "replicas (one independent lattice per GPU)"}
 
@@ -247,7 +250,7 @@ def time_precision(args, ld, phi_dev, precision, world, sample_clocks=False):
 
     n = args.size
     stream = torch.cuda.current_stream()
-    sim = ld.LdSim(n, n, n, precision=precision, stream=stream.cuda_stream)
+    sim = ld.LdSim(n, n, n, precision=precision, stream=stream.cuda_stream, stencil=args.stencil)
     sim.init(phi_dev)
     sim.step(args.warmup)
     totals = torch.empty(5, dtype=torch.float64, device="cuda")
@@ -290,7 +293,7 @@ def time_e2e(args, ld, phi_host_pinned, precision):
 
     n = args.size
     stream = torch.cuda.current_stream()
-    sim = ld.LdSim(n, n, n, precision=precision, stream=stream.cuda_stream)
+    sim = ld.LdSim(n, n, n, precision=precision, stream=stream.cuda_stream, stencil=args.stencil)
     phi_dev = torch.empty(phi_host_pinned.shape, dtype=torch.float64, device="cuda")
     phi_out_dev = torch.empty_like(phi_dev)
     phi_out_host = torch.empty(phi_host_pinned.shape, dtype=torch.float64, pin_memory=True)
@@ -325,7 +328,7 @@ def time_adjoint(args, ld, phi_dev, precision, steps=40, every=10):
 
     n = args.size
     stream = torch.cuda.current_stream()
-    sim = ld.LdSim(n, n, n, precision=precision, stream=stream.cuda_stream)
+    sim = ld.LdSim(n, n, n, precision=precision, stream=stream.cuda_stream, stencil=args.stencil)
     sim.init(phi_dev)
     nbytes = ld.ld_state_bytes(sim.ctx)
     ckpts = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(steps // every)]
@@ -475,7 +478,7 @@ def main():
         # FP64 is bounded by the FP64 pipe: 2 FP64 instructions per clock per SM
         # (GB300: 1.25 TFLOP/s nominal FP64 with an FMA counted as 2 flops, at
         # 152 SMs x 2.07 GHz), times the SMs and the maximum SM clock seen.
-        ops = recorded_fp64_ops()
+        ops = recorded_fp64_ops() if args.stencil == 7 else None  # the record is for the default stencils
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         mhz = (P["clocks"] or {}).get("sm_max_mhz") or 2070.0
         peak_ops = 2.0 * sms * mhz * 1e6 / 1e9
@@ -500,7 +503,7 @@ def main():
     cfg = config_of(args)
     cfg["bytes_per_site_algorithmic"] = P["bytes_per_site"]
     cfg["precision"] = primary
-    traffic = recorded_traffic(primary, n)
+    traffic = recorded_traffic(primary, n) if args.stencil == 7 else None  # recorded for the default stencils
     line = {
         "metric": METRIC,
         "value": P["mlups"],
