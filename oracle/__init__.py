@@ -30,12 +30,15 @@ _lock = threading.Lock()
 _lib = None
 
 Q = 19
-# Parameter vector order used by every call; the last entry selects the
+# Parameter vector order used by every call; the last two entries select the
 # stencils (0: 7-point Laplacian and central difference, 1: 19-point
-# isotropic). Derivative directions cover the first seven.
-PARAM_NAMES = ("A", "B", "kappa", "Gamma", "tau_f", "tau_g", "rho0", "stencil")
-DEFAULT_PARAMS = dict(A=-0.0625, B=0.0625, kappa=0.04, Gamma=0.5, tau_f=1.0, tau_g=1.0, rho0=1.0, stencil=0.0)
+# isotropic) and the force form (0: -phi grad mu, 1: -div P). Derivative
+# directions cover the first seven.
+PARAM_NAMES = ("A", "B", "kappa", "Gamma", "tau_f", "tau_g", "rho0", "stencil", "force")
+DEFAULT_PARAMS = dict(A=-0.0625, B=0.0625, kappa=0.04, Gamma=0.5, tau_f=1.0, tau_g=1.0, rho0=1.0, stencil=0.0,
+                      force=0.0)
 STENCILS = {7: 0.0, 19: 1.0}
+FORCES = {"potential": 0.0, "stress": 1.0}
 
 
 def build(force: bool = False) -> str:
@@ -76,8 +79,9 @@ def _load():
         lib.orc_macros.argtypes = [i, i, i, P, P, P, P, P, P, P, P, P, P]
         lib.orc_step_tl.argtypes = [i, i, i, P, P, P, P, P, P, i]
         lib.orc_loss_jvp.argtypes = [i, i, i, P, P, P, P, P, i, P, P]
+        lib.orc_stress.argtypes = [i, i, i, P, P, P]
         for name in ("orc_laplacian", "orc_gradient", "orc_propagate", "orc_init", "orc_step",
-                     "orc_macros", "orc_step_tl", "orc_loss_jvp"):
+                     "orc_macros", "orc_step_tl", "orc_loss_jvp", "orc_stress"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -95,12 +99,12 @@ def _f64(a):
 
 
 def _prm(p):
-    """The 8-entry parameter vector the C side reads (a 7-entry one gets the
-    default stencil)."""
+    """The 9-entry parameter vector the C side reads (shorter ones get the
+    default selectors)."""
     p = _f64(p)
-    if p.shape == (7,):
-        p = np.concatenate([p, [0.0]])
-    assert p.shape == (8,), "parameter vector: A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil"
+    if p.shape in ((7,), (8,)):
+        p = np.concatenate([p, np.zeros(9 - p.shape[0])])
+    assert p.shape == (9,), "parameter vector: A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil, force"
     return p
 
 
@@ -110,12 +114,13 @@ def _check(rc, what):
 
 
 def param_vector(**overrides) -> np.ndarray:
-    """Parameter vector; ``stencil`` is given as 7 or 19."""
+    """Parameter vector; ``stencil`` is given as 7 or 19, ``force`` as
+    "potential" or "stress"."""
     p = dict(DEFAULT_PARAMS)
     for k, v in overrides.items():
         if k not in p:
             raise KeyError(k)
-        p[k] = STENCILS[int(v)] if k == "stencil" else float(v)
+        p[k] = STENCILS[int(v)] if k == "stencil" else (FORCES[v] if k == "force" else float(v))
     return np.array([p[k] for k in PARAM_NAMES], dtype=np.float64)
 
 
@@ -170,6 +175,16 @@ def gradient(h, stencil=7):
     nz, ny, nx = h.shape
     out = np.zeros((3,) + h.shape)
     _check(_load().orc_gradient(nx, ny, nz, int(STENCILS[stencil]), _ptr(h), _ptr(out)), "gradient")
+    return out
+
+
+def stress(phi, prm):
+    """Chemical stress P of a (nz, ny, nx) phi field -> (6, nz, ny, nx), components
+    xx, yy, zz, xy, xz, yz, with the stencils selected in prm."""
+    phi = _f64(phi)
+    nz, ny, nx = phi.shape
+    out = np.zeros((6,) + phi.shape)
+    _check(_load().orc_stress(nx, ny, nz, _ptr(_prm(prm)), _ptr(phi), _ptr(out)), "stress")
     return out
 
 

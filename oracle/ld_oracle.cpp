@@ -23,6 +23,12 @@
 //       lap h = sum_i 6 w_i (h(x + c_i) - h(x)),
 //       grad h = sum_i 3 w_i c_i h(x + c_i),
 //     whose leading truncation errors are isotropic (sum_i w_i c c c c is);
+//   * optionally (force = 1) the force as the divergence of the chemical
+//     stress of the same free energy, F = -div P with
+//       P_ab = [p_b - kappa phi lap(phi) - kappa/2 |grad phi|^2] delta_ab
+//              + kappa d_a phi d_b phi,   p_b = A phi^2/2 + 3 B phi^4/4,
+//     equal to -phi grad(mu) in the continuum and conserving total momentum
+//     exactly on the lattice (a discrete divergence telescopes);
 //   * propagation: f_i(x + c_i, t+1) = f*_i(x, t) on a periodic lattice.
 // One step is: moments -> phi stencil and mu -> force and velocity ->
 // collide f -> collide g -> propagate, all stencils on fields of the same
@@ -98,6 +104,7 @@ template <class T>
 struct Params {
     T A, B, kappa, Gamma, tau_f, tau_g, rho0;
     int stencil;  // 0: 7-point / central difference; 1: 19-point isotropic
+    int force;    // 0: F = -phi grad(mu); 1: F = -div P (chemical stress)
 };
 
 struct Lattice {
@@ -249,9 +256,52 @@ void propagate_reverse(const Lattice& L, const T* in, T* out) {
     }
 }
 
+// Chemical stress of the phi^4 free energy at every site, six components
+// [xx, yy, zz, xy, xz, yz] of P (layout [c*N + s]), from grad phi and
+// lap(phi) with the selected stencils:
+//   iso = A/2 phi^2 + 3B/4 phi^4 - kappa phi lap - kappa/2 |grad phi|^2,
+//   P_aa = iso + kappa (d_a phi)^2,  P_ab = kappa d_a phi d_b phi.
+template <class T>
+void chemical_stress(const Lattice& L, const Params<T>& p, const T* phi, const T* lap, T* P) {
+    const long n = L.n;
+    std::vector<T> gr(3 * n);
+    gradient(L, phi, gr.data(), p.stencil);
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < n; ++s) {
+        const T ph = phi[s], gx = gr[s], gy = gr[n + s], gz = gr[2 * n + s];
+        const T pb = 0.5 * p.A * ph * ph + 0.75 * p.B * ph * ph * ph * ph;
+        const T iso = pb - p.kappa * ph * lap[s] - 0.5 * p.kappa * (gx * gx + gy * gy + gz * gz);
+        P[0 * n + s] = iso + p.kappa * gx * gx;
+        P[1 * n + s] = iso + p.kappa * gy * gy;
+        P[2 * n + s] = iso + p.kappa * gz * gz;
+        P[3 * n + s] = p.kappa * gx * gy;
+        P[4 * n + s] = p.kappa * gx * gz;
+        P[5 * n + s] = p.kappa * gy * gz;
+    }
+}
+
+// F_a = -sum_b D_b P_ab, D the selected gradient stencil, summed in the
+// order b = x, y, z.
+template <class T>
+void stress_force(const Lattice& L, const Params<T>& p, const T* P, T* F) {
+    const long n = L.n;
+    // component of P for the pair (a, b)
+    const int comp[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+    std::vector<T> d(3 * n);
+    std::vector<T> acc(3 * n, T(0.0));
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            gradient(L, P + comp[a][b] * n, d.data(), p.stencil);
+#pragma omp parallel for schedule(static)
+            for (long s = 0; s < n; ++s) acc[a * n + s] = acc[a * n + s] + d[b * n + s];
+        }
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < 3 * n; ++k) F[k] = -acc[k];
+}
+
 // Macroscopic fields of a pre-collision state, in the order the step uses
-// them: rho, j, phi; lap(phi) and mu; grad(mu), F = -phi grad(mu),
-// u = (j + F/2)/rho.
+// them: rho, j, phi; lap(phi) and mu; the force (F = -phi grad(mu), or
+// -div P); u = (j + F/2)/rho.
 template <class T>
 struct Macro {
     std::vector<T> rho, j, phi, lap, mu, gradmu, F, u;
@@ -281,10 +331,15 @@ void macroscopic(const Lattice& L, const Params<T>& p, const T* f, const T* g, M
     }
     chemical_potential(L, p, m.phi.data(), m.lap.data(), m.mu.data());
     gradient(L, m.mu.data(), m.gradmu.data(), p.stencil);
+    if (p.force == 1) {
+        std::vector<T> P(6 * n);
+        chemical_stress(L, p, m.phi.data(), m.lap.data(), P.data());
+        stress_force(L, p, P.data(), m.F.data());
+    }
 #pragma omp parallel for schedule(static)
     for (long s = 0; s < n; ++s)
         for (int a = 0; a < 3; ++a) {
-            m.F[a * n + s] = -m.phi[s] * m.gradmu[a * n + s];
+            if (p.force == 0) m.F[a * n + s] = -m.phi[s] * m.gradmu[a * n + s];
             m.u[a * n + s] = (m.j[a * n + s] + m.F[a * n + s] / 2.0) / m.rho[s];
         }
 }
@@ -350,9 +405,11 @@ void init_state(const Lattice& L, const Params<T>& p, const T* phi, const T* rho
     }
 }
 
-// prm = {A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil}; stencil 0 or 1.
+// prm = {A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil, force}; the last
+// two are selectors (0 or 1).
 Params<double> params_from(const double* prm) {
-    return Params<double>{prm[0], prm[1], prm[2], prm[3], prm[4], prm[5], prm[6], prm[7] != 0.0 ? 1 : 0};
+    return Params<double>{prm[0], prm[1], prm[2], prm[3], prm[4], prm[5], prm[6],
+                          prm[7] != 0.0 ? 1 : 0, prm[8] != 0.0 ? 1 : 0};
 }
 
 Params<Dual> dual_params_from(const double* prm, const double* dprm) {
@@ -364,7 +421,8 @@ Params<Dual> dual_params_from(const double* prm, const double* dprm) {
     p.tau_f = Dual(prm[4], dprm[4]);
     p.tau_g = Dual(prm[5], dprm[5]);
     p.rho0 = Dual(prm[6], dprm[6]);
-    p.stencil = prm[7] != 0.0 ? 1 : 0;  // not a differentiated parameter
+    p.stencil = prm[7] != 0.0 ? 1 : 0;  // selectors, not differentiated
+    p.force = prm[8] != 0.0 ? 1 : 0;
     return p;
 }
 
@@ -388,12 +446,24 @@ double plane_ordered_sum(const Lattice& L, const double* a) {
 
 // ---------------------------------------------------------------------------
 // C interface (called from Python through ctypes by the tests only).
-// prm = {A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil}; the derivative
-// direction dprm has the first seven. Return 0 on success, -1 on bad
-// arguments.
+// prm = {A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil, force}; the
+// derivative direction dprm has the first seven. Return 0 on success, -1 on
+// bad arguments.
 extern "C" {
 
-int orc_version() { return 2; }
+int orc_version() { return 3; }
+
+// Chemical stress P (6 x N, [xx, yy, zz, xy, xz, yz]) of a phi field with the
+// stencils and parameters of prm.
+int orc_stress(int nx, int ny, int nz, const double* prm, const double* phi, double* P) {
+    if (!dims_ok(nx, ny, nz) || !prm || !phi || !P) return -1;
+    Lattice L(nx, ny, nz);
+    Params<double> p = params_from(prm);
+    std::vector<double> lap(L.n);
+    laplacian(L, phi, lap.data(), p.stencil);
+    chemical_stress(L, p, phi, lap.data(), P);
+    return 0;
+}
 
 void orc_set_threads(int n) {
 #ifdef _OPENMP

@@ -543,3 +543,89 @@ def test_step_uses_selected_stencils(orc, stencil):
     assert np.abs(m["grad_phi"] - orc.gradient(phi, stencil)).max() < 1e-16
     other = 19 if stencil == 7 else 7
     assert np.abs(m["mu"] - (A * phi + B * phi ** 3 - kappa * orc.laplacian(phi, other))).max() > 1e-4
+
+
+# --------------------------------------------------------------------------
+# Force as the divergence of the chemical stress (catches a wrong bulk
+# pressure, a missing -kappa phi lap(phi) or -kappa/2 |grad phi|^2 term, a
+# transposed or non-symmetric stress, a divergence taken over the wrong
+# index, and a step that ignores the force selection).
+
+
+def test_stress_of_uniform_phi(orc):
+    """No gradients: P = p_b I with the bulk pressure p_b = phi f'(phi) - f
+    of f = A phi^2/2 + B phi^4/4, i.e. A phi^2/2 + 3 B phi^4/4."""
+    prm = orc.param_vector(A=-0.07, B=0.09)
+    A, B = prm[0], prm[1]
+    phi = np.full((4, 5, 6), 0.61)
+    P = orc.stress(phi, prm)
+    pb = 0.5 * A * 0.61 ** 2 + 0.75 * B * 0.61 ** 4
+    for c in range(3):
+        assert np.abs(P[c] - pb).max() < 1e-16
+    assert np.abs(P[3:]).max() == 0.0
+
+
+@pytest.mark.parametrize("stencil", [7, 19])
+def test_stress_of_a_field_varying_along_x(orc, stencil):
+    """phi(x) only: the off-diagonal stress vanishes, P_yy = P_zz, and
+    P_xx - P_yy = kappa (d_x phi)^2 with the selected gradient."""
+    prm = orc.param_vector(kappa=0.06, stencil=stencil)
+    phi = _axis_field((5, 6, 16), 2, seed=8)
+    P = orc.stress(phi, prm)
+    gx = orc.gradient(phi, stencil)[0]
+    assert np.abs(P[3:]).max() < 1e-17
+    assert np.abs(P[1] - P[2]).max() < 1e-17
+    assert np.abs((P[0] - P[1]) - 0.06 * gx * gx).max() < 1e-15
+
+
+@pytest.mark.parametrize("stencil", [7, 19])
+def test_stress_force_sums_to_zero_and_conserves_momentum(orc, stencil):
+    """On a periodic lattice a discrete divergence telescopes: sum_x F = 0,
+    so the Guo step conserves total momentum exactly, over many steps. The
+    potential form -phi grad(mu) has no such property."""
+    nz, ny, nx = 6, 7, 8
+    phi = inputs.spinodal_phi(nx, ny, nz, seed=33, amplitude=0.5)
+    stress = orc.param_vector(force="stress", stencil=stencil, kappa=0.06)
+    pot = orc.param_vector(stencil=stencil, kappa=0.06)
+    f, g = orc.init(phi, stress)
+    m = orc.macros(f, g, stress)
+    assert np.abs(m["force"].reshape(3, -1).sum(1)).max() < 1e-15
+    mp = orc.macros(*orc.init(phi, pot), pot)
+    assert np.abs(mp["force"].reshape(3, -1).sum(1)).max() > 1e-6
+    j0 = m["totals"][2:].copy()
+    f, g = orc.step(f, g, stress, 50)
+    j1 = orc.macros(f, g, stress)["totals"][2:]
+    assert np.abs(j1 - j0).max() < 1e-13
+
+
+def test_stress_force_converges_to_potential_form(orc):
+    """div P = phi grad(mu) in the continuum (Gibbs-Duhem): for the same smooth
+    field sampled twice as finely (kappa and the lattice spacing scaled
+    together), the difference of the two discrete forces falls by about 4."""
+    def gap(n):
+        prm_s = orc.param_vector(force="stress", kappa=0.04 * (n / 32) ** 2)
+        prm_p = orc.param_vector(kappa=0.04 * (n / 32) ** 2)
+        z, y, x = np.meshgrid(np.arange(4), np.arange(n), np.arange(n), indexing="ij")
+        phi = 0.6 * np.sin(2 * math.pi * x / n) * np.cos(2 * math.pi * y / n)
+        fs = orc.macros(*orc.init(phi, prm_s), prm_s)["force"]
+        fp = orc.macros(*orc.init(phi, prm_p), prm_p)["force"]
+        return np.abs(fs - fp).max() / np.abs(fp).max()
+    g32, g64 = gap(32), gap(64)
+    assert g32 < 0.05
+    assert 3.0 < g32 / g64 < 5.0
+
+
+def test_tangent_linear_with_stress_force(orc):
+    nz, ny, nx = 5, 6, 4
+    prm = orc.param_vector(tau_f=0.9, force="stress")
+    phi0 = inputs.spinodal_phi(nx, ny, nz, seed=21, amplitude=0.3)
+    target = inputs.spinodal_phi(nx, ny, nz, seed=22, amplitude=0.3)
+    dphi = np.random.default_rng(6).standard_normal(phi0.shape)
+    dprm = np.zeros(9)
+    dprm[2], dprm[4] = 0.3, -0.7
+    steps = 6
+    _, dL = orc.loss_jvp(phi0, target, prm, steps, dphi0=dphi, dprm=dprm)
+    h = 1e-5
+    fd = (orc.loss(phi0 + h * dphi, target, prm + h * dprm, steps) -
+          orc.loss(phi0 - h * dphi, target, prm - h * dprm, steps)) / (2 * h)
+    assert dL == pytest.approx(fd, rel=1e-7)
