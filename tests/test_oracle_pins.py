@@ -399,7 +399,7 @@ def test_tangent_linear_matches_finite_differences(orc, stencil):
     target = inputs.spinodal_phi(nx, ny, nz, seed=22, amplitude=0.3)
     rng = np.random.default_rng(5)
     dphi = rng.standard_normal(phi0.shape)
-    dprm = np.zeros(8)  # the stencil entry is not differentiated
+    dprm = np.zeros(len(prm))  # the selector entries are not differentiated
     dprm[2] = 0.3  # kappa
     dprm[4] = -0.7  # tau_f
     steps = 6
