@@ -75,6 +75,19 @@ enum { LD_KERNEL_AUTO = 0, LD_KERNEL_GENERIC = 1, LD_KERNEL_FUSED = 2, LD_KERNEL
  *   FUSED kernels only (LD_EINVAL with LD_KERNEL_FUSED_TMA). */
 enum { LD_STENCIL_7 = 0, LD_STENCIL_19 = 1 };
 
+/* Form of the force on the fluid (the "Chemical stress" kernel of a Ludwig
+ * timestep, Sec. 2.1.1 of the paper, which gives no formula).
+ * LD_FORCE_POTENTIAL: F = -phi grad(mu) (default).
+ * LD_FORCE_STRESS: F = -div P, the divergence of the chemical stress
+ *   P_ab = [A phi^2/2 + 3B phi^4/4 - kappa phi lap(phi) - kappa/2 |grad phi|^2] delta_ab
+ *          + kappa d_a phi d_b phi,
+ *   with the selected stencils; equal to -phi grad(mu) in the continuum, it
+ *   conserves total momentum exactly on the lattice. GENERIC kernel only
+ *   (AUTO picks it; FUSED and FUSED_TMA give LD_EINVAL); no adjoint
+ *   (ld_adjoint_workspace_bytes returns 0, ld_adjoint_attach LD_EINVAL).
+ *   Fixed at ld_create (its 6 stress fields are part of the workspace). */
+enum { LD_FORCE_POTENTIAL = 0, LD_FORCE_STRESS = 1 };
+
 enum {
     LD_OK = 0,
     LD_EINVAL = -1,     /* bad argument: dims < 4, null/host pointer, tau <= 1/2, small workspace */
@@ -90,6 +103,7 @@ typedef struct {
     int precision;             /* LD_FP64 .. LD_BF16DEV */
     int kernel;                /* LD_KERNEL_AUTO / GENERIC / FUSED / FUSED_TMA */
     int stencil;               /* LD_STENCIL_7 / LD_STENCIL_19 */
+    int force;                 /* LD_FORCE_POTENTIAL / LD_FORCE_STRESS */
 } ld_params;
 
 typedef struct ld_ctx ld_ctx;

@@ -33,10 +33,10 @@ size_t real_bytes_of(int prec) { return prec == LD_FP64 ? 8 : 4; }
 long long npad_of(long long n) { return (n + 63) / 64 * 64; }
 
 struct Layout {
-    size_t dist, phi, mu, partials, totals, ref, status, total;
+    size_t dist, phi, mu, stress, partials, totals, ref, status, total;
 };
 
-Layout layout_of(int nx, int ny, int nz, int prec) {
+Layout layout_of(int nx, int ny, int nz, int prec, int force) {
     const long long npad = npad_of((long long)nx * ny * nz);
     Layout L;
     size_t off = 0;
@@ -47,6 +47,8 @@ Layout layout_of(int nx, int ny, int nz, int prec) {
     off += align_up(npad * real_bytes_of(prec));
     L.mu = off;
     off += align_up(npad * real_bytes_of(prec));
+    L.stress = off;  // six stress fields, only for the stress form of the force
+    if (force == LD_FORCE_STRESS) off += align_up(6 * npad * real_bytes_of(prec));
     L.partials = off;
     off += align_up(sizeof(double) * ld::kRedBlocks * ld::kRedFields);
     L.totals = off;
@@ -84,6 +86,9 @@ bool params_ok(const ld_params* p, const char** why) {
     if (p->stencil != LD_STENCIL_7 && p->stencil != LD_STENCIL_19) return *why = "unknown stencil", false;
     if (p->stencil == LD_STENCIL_19 && p->kernel == LD_KERNEL_FUSED_TMA)
         return *why = "the TMA-staged kernel has the 7-point stencils only", false;
+    if (p->force != LD_FORCE_POTENTIAL && p->force != LD_FORCE_STRESS) return *why = "unknown force form", false;
+    if (p->force == LD_FORCE_STRESS && (p->kernel == LD_KERNEL_FUSED || p->kernel == LD_KERNEL_FUSED_TMA))
+        return *why = "the stress form of the force runs on the generic kernel only", false;
     return true;
 }
 
@@ -133,7 +138,7 @@ extern "C" {
 size_t ld_workspace_bytes(int nx, int ny, int nz, const ld_params* p) {
     const char* why = nullptr;
     if (!dims_ok(nx, ny, nz) || !params_ok(p, &why)) return 0;
-    return layout_of(nx, ny, nz, p->precision).total;
+    return layout_of(nx, ny, nz, p->precision, p->force).total;
 }
 
 int ld_create(int nx, int ny, int nz, const ld_params* p, void* dev_workspace, size_t bytes, void* cuda_stream,
@@ -143,12 +148,15 @@ int ld_create(int nx, int ny, int nz, const ld_params* p, void* dev_workspace, s
     *out = nullptr;
     if (!dims_ok(nx, ny, nz)) return fail(nullptr, LD_EINVAL, "lattice %dx%dx%d: each dim must be >= 4", nx, ny, nz);
     if (!params_ok(p, &why)) return fail(nullptr, LD_EINVAL, "%s", why);
-    const Layout L = layout_of(nx, ny, nz, p->precision);
+    const Layout L = layout_of(nx, ny, nz, p->precision, p->force);
     if (!is_device_ptr(dev_workspace)) return fail(nullptr, LD_EINVAL, "workspace is not a device pointer");
     if ((uintptr_t)dev_workspace % kAlign) return fail(nullptr, LD_EINVAL, "workspace must be 256-byte aligned");
     if (bytes < L.total)
         return fail(nullptr, LD_EINVAL, "workspace of %zu bytes is smaller than the %zu needed", bytes, L.total);
-    const int step_kernel = ld::choose_step_kernel(nx, ny, nz, p->precision, p->kernel);
+    // the stress form of the force runs on the generic kernel
+    const int step_kernel = p->force == LD_FORCE_STRESS
+                                ? ld::kStepGeneric
+                                : ld::choose_step_kernel(nx, ny, nz, p->precision, p->kernel);
     if (step_kernel == 0)
         return fail(nullptr, LD_EINVAL,
                     "fused kernels need nx %% 32 == 0, ny %% 8 == 0, nz %% 4 == 0 (TMA: FP32/FP16DEV/BF16DEV only)");
@@ -172,6 +180,7 @@ int ld_create(int nx, int ny, int nz, const ld_params* p, void* dev_workspace, s
     c->cur = 0;
     c->phi = c->ws + L.phi;
     c->mu = c->ws + L.mu;
+    c->stress = p->force == LD_FORCE_STRESS ? c->ws + L.stress : nullptr;
     c->partials = (double*)(c->ws + L.partials);
     c->totals = (double*)(c->ws + L.totals);
     c->ref = (float*)(c->ws + L.ref);
@@ -214,8 +223,9 @@ int ld_set_params(ld_ctx* c, const ld_params* p) {
     const char* why = nullptr;
     if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
     if (!params_ok(p, &why)) return fail(c, LD_EINVAL, "%s", why);
-    if (p->precision != c->prm.precision || p->kernel != c->prm.kernel || p->rho0 != c->prm.rho0)
-        return fail(c, LD_EINVAL, "precision, kernel and rho0 are fixed at ld_create");
+    if (p->precision != c->prm.precision || p->kernel != c->prm.kernel || p->rho0 != c->prm.rho0 ||
+        p->force != c->prm.force)
+        return fail(c, LD_EINVAL, "precision, kernel, rho0 and the force form are fixed at ld_create");
     c->prm = *p;
     return LD_OK;
 }
@@ -368,10 +378,14 @@ int check_adj(ld_ctx* c) {
 
 extern "C" {
 
-size_t ld_adjoint_workspace_bytes(const ld_ctx* c) { return c ? adj_layout_of(c).total : 0; }
+size_t ld_adjoint_workspace_bytes(const ld_ctx* c) {
+    return c && c->prm.force == LD_FORCE_POTENTIAL ? adj_layout_of(c).total : 0;
+}
 
 int ld_adjoint_attach(ld_ctx* c, void* dev_workspace, size_t bytes) {
     if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
+    if (c->prm.force != LD_FORCE_POTENTIAL)
+        return fail(c, LD_EINVAL, "the adjoint is built for the force F = -phi grad(mu) only");
     const AdjLayout L = adj_layout_of(c);
     if (!is_device_ptr(dev_workspace)) return fail(c, LD_EINVAL, "adjoint workspace is not a device pointer");
     if ((uintptr_t)dev_workspace % kAlign) return fail(c, LD_EINVAL, "adjoint workspace must be 256-byte aligned");

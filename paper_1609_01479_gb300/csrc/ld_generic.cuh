@@ -96,6 +96,81 @@ __global__ void __launch_bounds__(kRowThreads) k_mu(RowGeom rg, Model<R> m, cons
     mu[s] = chem_potential(phi[s], nb, m);
 }
 
+// Neighbour offsets of a row-ordered site (periodic).
+struct RowNbr {
+    int xp, xm, yp, ym, zp, zm;
+    __device__ __forceinline__ int of(int i) const {
+        return (cx(i) > 0 ? xp : (cx(i) < 0 ? xm : 0)) + (cy(i) > 0 ? yp : (cy(i) < 0 ? ym : 0)) +
+               (cz(i) > 0 ? zp : (cz(i) < 0 ? zm : 0));
+    }
+};
+__device__ __forceinline__ RowNbr row_nbr(const RowGeom& rg, int x, int y, int z) {
+    const int nx = rg.nx, plane = rg.nx * rg.ny;
+    return RowNbr{x + 1 == nx ? 1 - nx : 1,
+                  x == 0 ? nx - 1 : -1,
+                  y + 1 == rg.ny ? (1 - rg.ny) * nx : nx,
+                  y == 0 ? (rg.ny - 1) * nx : -nx,
+                  z + 1 == rg.nz ? (1 - rg.nz) * plane : plane,
+                  z == 0 ? (rg.nz - 1) * plane : -plane};
+}
+
+// Gradient of a field at s with the selected stencils (7-point: central
+// difference; 19-point: grad19), in the type of the field.
+template <class T>
+__device__ __forceinline__ void grad_at(int iso, const T* h, int s, const RowNbr& o, T& gx, T& gy, T& gz) {
+    if (iso) {
+        auto nb = [&](int i) { return h[s + o.of(i)]; };
+        grad19(nb, gx, gy, gz);
+    } else {
+        gx = T(0.5) * (h[s + o.xp] - h[s + o.xm]);
+        gy = T(0.5) * (h[s + o.yp] - h[s + o.ym]);
+        gz = T(0.5) * (h[s + o.zp] - h[s + o.zm]);
+    }
+}
+
+// Stage 2b (LD_FORCE_STRESS): chemical stress P[6][npad] (xx, yy, zz, xy,
+// xz, yz) from grad phi and lap(phi) with the selected stencils:
+//   iso = A/2 phi^2 + 3B/4 phi^4 - kappa phi lap - kappa/2 |grad phi|^2,
+//   P_aa = iso + kappa (d_a phi)^2, P_ab = kappa d_a phi d_b phi,
+// each expression in that operation order.
+template <class R, class I>
+__global__ void __launch_bounds__(kRowThreads) k_stress(RowGeom rg, I npad, Model<R> m, const R* __restrict__ phi,
+                                                        R* __restrict__ P) {
+    int x, y, z, s;
+    if (!row_site(rg, blockIdx.x, x, y, z, s)) return;
+    const RowNbr o = row_nbr(rg, x, y, z);
+    const R ph = phi[s];
+    R gx, gy, gz, lap;
+    grad_at(m.iso, phi, s, o, gx, gy, gz);
+    if (m.iso) {
+        auto nb = [&](int i) { return phi[s + o.of(i)]; };
+        lap = lap19(ph, nb);
+    } else {
+        lap = phi[s + o.xp] + phi[s + o.xm] + phi[s + o.yp] + phi[s + o.ym] + phi[s + o.zp] + phi[s + o.zm] - R(6) * ph;
+    }
+    const R pb = R(0.5) * m.A * ph * ph + R(0.75) * m.B * ph * ph * ph * ph;
+    const R iso = pb - m.kappa * ph * lap - R(0.5) * m.kappa * (gx * gx + gy * gy + gz * gz);
+    P[s] = iso + m.kappa * gx * gx;
+    P[npad + s] = iso + m.kappa * gy * gy;
+    P[2 * npad + s] = iso + m.kappa * gz * gz;
+    P[3 * npad + s] = m.kappa * gx * gy;
+    P[4 * npad + s] = m.kappa * gx * gz;
+    P[5 * npad + s] = m.kappa * gy * gz;
+}
+
+// F = -div P at s: F_a = -((D_x P_ax + D_y P_ay) + D_z P_az), D the selected
+// gradient, components of P indexed xx 0, yy 1, zz 2, xy 3, xz 4, yz 5.
+template <class T, class I>
+__device__ __forceinline__ void stress_force_at(int iso, const T* P, I npad, int s, const RowNbr& o, T& Fx, T& Fy,
+                                                T& Fz) {
+    T d[6][3];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) grad_at(iso, P + c * npad, s, o, d[c][0], d[c][1], d[c][2]);
+    Fx = -((d[0][0] + d[3][1]) + d[4][2]);
+    Fy = -((d[3][0] + d[1][1]) + d[5][2]);
+    Fz = -((d[4][0] + d[5][1]) + d[2][2]);
+}
+
 // Resident blocks per SM the collision kernel is compiled for: 6 x 128
 // threads (80 registers) with FP32 arithmetic, 3 with FP64.
 template <int P>
@@ -110,7 +185,8 @@ __global__ void __launch_bounds__(kRowThreads, rows_blocks_per_sm<P>())
     k_collide(RowGeom rg, I npad, Model<typename Prec<P>::real_t> m, const typename Prec<P>::store_t* __restrict__ fs,
               const typename Prec<P>::store_t* __restrict__ gs, typename Prec<P>::store_t* __restrict__ fd,
               typename Prec<P>::store_t* __restrict__ gd, const typename Prec<P>::real_t* __restrict__ phi,
-              const typename Prec<P>::real_t* __restrict__ mu, const float* __restrict__ ref) {
+              const typename Prec<P>::real_t* __restrict__ mu, const float* __restrict__ ref,
+              const typename Prec<P>::real_t* __restrict__ stress) {
     using R = typename Prec<P>::real_t;
     using S = typename Prec<P>::store_t;
     __shared__ float refs[2 * Q];  // codec references, read once per block
@@ -133,19 +209,15 @@ __global__ void __launch_bounds__(kRowThreads, rows_blocks_per_sm<P>())
     const int ozp = z + 1 == rg.nz ? (1 - rg.nz) * plane : plane, ozm = z == 0 ? (rg.nz - 1) * plane : -plane;
 
     const R ph = phi[s], muc = mu[s];
-    R gmx, gmy, gmz;
-    if (m.iso) {
-        auto nb = [&](int i) {
-            return mu[s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
-                      (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0))];
-        };
-        grad19(nb, gmx, gmy, gmz);
-    } else {
-        gmx = R(0.5) * (mu[s + oxp] - mu[s + oxm]);
-        gmy = R(0.5) * (mu[s + oyp] - mu[s + oym]);
-        gmz = R(0.5) * (mu[s + ozp] - mu[s + ozm]);
+    const RowNbr o{oxp, oxm, oyp, oym, ozp, ozm};
+    R Fx, Fy, Fz;
+    if (stress) {  // F = -div P
+        stress_force_at(m.iso, stress, npad, s, o, Fx, Fy, Fz);
+    } else {  // F = -phi grad(mu)
+        R gmx, gmy, gmz;
+        grad_at(m.iso, mu, s, o, gmx, gmy, gmz);
+        Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
     }
-    const R Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
 
     R f[Q];
     R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
@@ -330,7 +402,7 @@ __global__ void __launch_bounds__(kThreads)
              const typename Prec<P>::store_t* __restrict__ gs, const typename Prec<P>::real_t* __restrict__ phis,
              const typename Prec<P>::real_t* __restrict__ mu, const float* __restrict__ ref,
              double* __restrict__ rho_out, double* __restrict__ u_out, double* __restrict__ phi_out,
-             double* __restrict__ gphi_out, int iso) {
+             double* __restrict__ gphi_out, int iso, const typename Prec<P>::real_t* __restrict__ stress) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.n) return;
     int x, y, z;
@@ -365,9 +437,18 @@ __global__ void __launch_bounds__(kThreads)
         }
     };
     if (u_out) {
-        double gx, gy, gz;
-        grad(mu, gx, gy, gz);
-        const double Fx = -ph * gx, Fy = -ph * gy, Fz = -ph * gz;
+        double Fx, Fy, Fz;
+        if (stress) {  // F = -div P
+            double d[6][3];
+            for (int c = 0; c < 6; ++c) grad(stress + c * g.npad, d[c][0], d[c][1], d[c][2]);
+            Fx = -((d[0][0] + d[3][1]) + d[4][2]);
+            Fy = -((d[3][0] + d[1][1]) + d[5][2]);
+            Fz = -((d[4][0] + d[5][1]) + d[2][2]);
+        } else {  // F = -phi grad(mu)
+            double gx, gy, gz;
+            grad(mu, gx, gy, gz);
+            Fx = -ph * gx, Fy = -ph * gy, Fz = -ph * gz;
+        }
         u_out[s] = (jx + 0.5 * Fx) / rho;
         u_out[g.n + s] = (jy + 0.5 * Fy) / rho;
         u_out[2 * g.n + s] = (jz + 0.5 * Fz) / rho;
@@ -464,9 +545,12 @@ cudaError_t collide_rows(ld_ctx* c, const void* src, void* dst, void* fields) {
     if (e != cudaSuccess) return e;
     const R* phi = fields ? (const R*)fields : (const R*)c->phi;
     const R* mu = fields ? (const R*)fields + c->geom.npad : (const R*)c->mu;
+    if (c->stress)
+        k_stress<R, I><<<row_blocks(c->geom), kRowThreads, 0, c->stream>>>(row_geom(c->geom), (I)c->geom.npad,
+                                                                           model_of<R>(c->prm), phi, (R*)c->stress);
     k_collide<P, I><<<row_blocks(c->geom), kRowThreads, 0, c->stream>>>(
         row_geom(c->geom), (I)c->geom.npad, model_of<R>(c->prm), (const S*)f_part(c, src), (const S*)g_part(c, src),
-        (S*)f_part(c, dst), (S*)g_part(c, dst), phi, mu, c->ref);
+        (S*)f_part(c, dst), (S*)g_part(c, dst), phi, mu, c->ref, (const R*)c->stress);
     return cudaGetLastError();
 }
 
@@ -483,9 +567,18 @@ cudaError_t macros_p(ld_ctx* c, double* rho, double* u, double* phi, double* gph
     const Geom g = to_dev(c->geom);
     cudaError_t e = phi_mu_p<P>(c, c->dist[c->cur]);
     if (e != cudaSuccess) return e;
+    if (c->stress) {
+        if (offsets_fit_int(c))
+            k_stress<R, int><<<row_blocks(c->geom), kRowThreads, 0, c->stream>>>(
+                row_geom(c->geom), (int)g.npad, model_of<R>(c->prm), (const R*)c->phi, (R*)c->stress);
+        else
+            k_stress<R, long long><<<row_blocks(c->geom), kRowThreads, 0, c->stream>>>(
+                row_geom(c->geom), (long long)g.npad, model_of<R>(c->prm), (const R*)c->phi, (R*)c->stress);
+    }
     k_macros<P><<<blocks_for(g.n), kThreads, 0, c->stream>>>(g, (const S*)f_of(c, c->cur), (const S*)g_of(c, c->cur),
                                                              (const R*)c->phi, (const R*)c->mu, c->ref, rho, u,
-                                                             phi, gphi, c->prm.stencil == LD_STENCIL_19);
+                                                             phi, gphi, c->prm.stencil == LD_STENCIL_19,
+                                                             (const R*)c->stress);
     return cudaGetLastError();
 }
 

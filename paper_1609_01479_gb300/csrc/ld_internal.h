@@ -41,6 +41,7 @@ struct ld_ctx {
     int cur;        // index of the buffer holding the current state
     void* phi;      // real_t[npad] scratch
     void* mu;       // real_t[npad] scratch
+    void* stress;   // real_t[6][npad] chemical stress (LD_FORCE_STRESS), else NULL
     double* partials;  // kRedBlocks * kRedFields doubles
     double* totals;    // 8 doubles scratch
     float* ref;        // 38 floats: f then g deviation references

@@ -29,6 +29,8 @@ KERNELS = {"auto": LD_KERNEL_AUTO, "generic": LD_KERNEL_GENERIC, "fused": LD_KER
 STORE_BYTES = {LD_FP64: 8, LD_FP32: 4, LD_FP16DEV: 2, LD_BF16DEV: 2}
 LD_STENCIL_7, LD_STENCIL_19 = 0, 1
 STENCILS = {7: LD_STENCIL_7, 19: LD_STENCIL_19}
+LD_FORCE_POTENTIAL, LD_FORCE_STRESS = 0, 1
+FORCES = {"potential": LD_FORCE_POTENTIAL, "stress": LD_FORCE_STRESS}
 Q = 19
 
 
@@ -36,7 +38,7 @@ class LdParams(ctypes.Structure):
     _fields_ = [("A", ctypes.c_double), ("B", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("Gamma", ctypes.c_double), ("tau_f", ctypes.c_double), ("tau_g", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("stencil", ctypes.c_int)]
+                ("stencil", ctypes.c_int), ("force", ctypes.c_int)]
 
 
 class LdError(RuntimeError):
@@ -119,12 +121,14 @@ def _call(name, ctx, *args):
 
 
 def make_params(A=-0.0625, B=0.0625, kappa=0.04, Gamma=0.5, tau_f=1.0, tau_g=1.0, rho0=1.0,
-                precision="fp32", kernel="auto", stencil=7) -> LdParams:
+                precision="fp32", kernel="auto", stencil=7, force="potential") -> LdParams:
     """ld_params; stencil is 7 (7-point Laplacian, central difference) or 19
-    (the 19-point isotropic forms)."""
+    (the 19-point isotropic forms); force is "potential" (-phi grad mu) or
+    "stress" (-div P)."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     kern = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-    return LdParams(A, B, kappa, Gamma, tau_f, tau_g, rho0, prec, kern, STENCILS[int(stencil)])
+    frc = FORCES[force] if isinstance(force, str) else int(force)
+    return LdParams(A, B, kappa, Gamma, tau_f, tau_g, rho0, prec, kern, STENCILS[int(stencil)], frc)
 
 
 # ---------------------------------------------------------------------------
@@ -289,6 +293,8 @@ class LdSim:
         kw = {f[0]: getattr(p, f[0]) for f in LdParams._fields_}
         if "stencil" in model:
             model = dict(model, stencil=STENCILS[int(model["stencil"])])
+        if isinstance(model.get("force"), str):
+            model = dict(model, force=FORCES[model["force"]])
         kw.update(model)
         self.params = LdParams(*[kw[f[0]] for f in LdParams._fields_])
         ld_set_params(self.ctx, self.params)

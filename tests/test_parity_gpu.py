@@ -38,8 +38,10 @@ def rel_l2(a, b):
 def gpu_run(ld, phi, steps, precision="fp64", kernel="auto", prm=None, rho=None, u=None):
     nz, ny, nx = phi.shape
     model = {} if prm is None else dict(zip(oracle.PARAM_NAMES, map(float, prm)))
-    if "stencil" in model:  # the oracle's 0/1 selector -> the library's 7/19
+    if "stencil" in model:  # the oracle's 0/1 selectors -> the library's names
         model["stencil"] = 19 if model["stencil"] else 7
+    if "force" in model:
+        model["force"] = "stress" if model["force"] else "potential"
     sim = ld.LdSim(nx, ny, nz, precision=precision, kernel=kernel, **model)
     sim.init(torch.from_numpy(phi).cuda(),
              None if rho is None else torch.from_numpy(rho).cuda(),
@@ -141,6 +143,62 @@ def test_fp32_isotropic_stencils(ld, kernel):
     assert rel_l2(g["grad_phi"], r["grad_phi"]) <= 1e-4
     r7 = oracle_run(phi, 100)
     assert rel_l2(r7["phi"], r["phi"]) > 1e-4
+
+
+@pytest.mark.parametrize("stencil", [7, 19])
+@pytest.mark.parametrize("shape", [(7, 6, 5), (5, 9, 33), (8, 8, 32)])
+def test_fp64_stress_force(ld, shape, stencil):
+    """F = -div P (LD_FORCE_STRESS) on the generic launches: 1e-12 against
+    the oracle, on ragged and tiled lattices, with either stencil pair."""
+    nz, ny, nx = shape
+    phi = inputs.spinodal_phi(nx, ny, nz, seed=19, amplitude=0.4)
+    prm = oracle.param_vector(tau_f=0.9, tau_g=1.1, kappa=0.06, stencil=stencil, force="stress")
+    assert_parity(gpu_run(ld, phi, 20, prm=prm), oracle_run(phi, 20, prm=prm), FP64_TOL)
+
+
+def test_stress_force_conserves_momentum_on_the_gpu(ld):
+    """With F = -div P total momentum is conserved to rounding (FP64), where
+    -phi grad mu changes it at every step."""
+    nz, ny, nx = 16, 16, 32
+    phi = inputs.spinodal_phi(nx, ny, nz, seed=23, amplitude=0.5)
+    drift = {}
+    for force in ("stress", "potential"):
+        sim = ld.LdSim(nx, ny, nz, precision="fp64", force=force, kappa=0.06)
+        sim.init(torch.from_numpy(phi).cuda())
+        j0 = sim.totals().cpu().numpy()[2:]
+        sim.step(200)
+        j1 = sim.totals().cpu().numpy()[2:]
+        drift[force] = float(np.abs(j1 - j0).max())
+        sim.close()
+    assert drift["stress"] < 1e-11
+    assert drift["potential"] > 1e3 * drift["stress"]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16dev", 1e-2)])
+def test_reduced_precision_stress_force(ld, precision, tol):
+    nz, ny, nx = 32, 32, 32
+    phi = inputs.spinodal_phi(nx, ny, nz, seed=2)
+    prm = oracle.param_vector(force="stress")
+    g = gpu_run(ld, phi, 100, precision=precision, prm=prm)
+    r = oracle_run(phi, 100, prm=prm)
+    assert rel_l2(g["phi"], r["phi"]) <= tol
+
+
+def test_stress_force_refusals(ld):
+    """The stress form runs on the generic launches and has no adjoint."""
+    for kernel in ("fused", "fused_tma"):
+        with pytest.raises(ld.LdError) as e:
+            ld.LdSim(32, 8, 4, precision="fp32", kernel=kernel, force="stress")
+        assert e.value.code == ld.LD_EINVAL
+    sim = ld.LdSim(32, 8, 4, precision="fp32", force="stress")
+    assert ld.ld_adjoint_workspace_bytes(sim.ctx) == 0
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ld.LdError) as e:
+        ld.ld_adjoint_attach(sim.ctx, ws)
+    assert e.value.code == ld.LD_EINVAL
+    with pytest.raises(ld.LdError):
+        sim.set_params(force="potential")
+    sim.close()
 
 
 def test_isotropic_stencils_refused_by_the_tma_kernel(ld):
