@@ -30,13 +30,15 @@ _lock = threading.Lock()
 _lib = None
 
 Q = 19
-# Parameter vector order used by every call; the last two entries select the
-# stencils (0: 7-point Laplacian and central difference, 1: 19-point
-# isotropic) and the force form (0: -phi grad mu, 1: -div P). Derivative
-# directions cover the first seven.
-PARAM_NAMES = ("A", "B", "kappa", "Gamma", "tau_f", "tau_g", "rho0", "stencil", "force")
+# Parameter vector order used by every call; then selectors of the stencils
+# (0: 7-point Laplacian and central difference, 1: 19-point isotropic), the
+# force form (0: -phi grad mu, 1: -div P) and the f collision (0: BGK, 1:
+# two-relaxation-time), and the TRT magic parameter. Derivative directions
+# cover the first seven.
+PARAM_NAMES = ("A", "B", "kappa", "Gamma", "tau_f", "tau_g", "rho0", "stencil", "force", "collision", "magic")
 DEFAULT_PARAMS = dict(A=-0.0625, B=0.0625, kappa=0.04, Gamma=0.5, tau_f=1.0, tau_g=1.0, rho0=1.0, stencil=0.0,
-                      force=0.0)
+                      force=0.0, collision=0.0, magic=0.1875)
+COLLISIONS = {"bgk": 0.0, "trt": 1.0}
 STENCILS = {7: 0.0, 19: 1.0}
 FORCES = {"potential": 0.0, "stress": 1.0}
 
@@ -99,12 +101,12 @@ def _f64(a):
 
 
 def _prm(p):
-    """The 9-entry parameter vector the C side reads (shorter ones get the
-    default selectors)."""
+    """The 11-entry parameter vector the C side reads (shorter ones get the
+    defaults of the missing entries)."""
     p = _f64(p)
-    if p.shape in ((7,), (8,)):
-        p = np.concatenate([p, np.zeros(9 - p.shape[0])])
-    assert p.shape == (9,), "parameter vector: A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil, force"
+    if p.shape[0] < len(PARAM_NAMES):
+        p = np.concatenate([p, [DEFAULT_PARAMS[k] for k in PARAM_NAMES[p.shape[0]:]]])
+    assert p.shape == (len(PARAM_NAMES),), "parameter vector: " + ", ".join(PARAM_NAMES)
     return p
 
 
@@ -115,12 +117,13 @@ def _check(rc, what):
 
 def param_vector(**overrides) -> np.ndarray:
     """Parameter vector; ``stencil`` is given as 7 or 19, ``force`` as
-    "potential" or "stress"."""
+    "potential" or "stress", ``collision`` as "bgk" or "trt"."""
     p = dict(DEFAULT_PARAMS)
+    names = {"stencil": lambda v: STENCILS[int(v)], "force": lambda v: FORCES[v], "collision": lambda v: COLLISIONS[v]}
     for k, v in overrides.items():
         if k not in p:
             raise KeyError(k)
-        p[k] = STENCILS[int(v)] if k == "stencil" else (FORCES[v] if k == "force" else float(v))
+        p[k] = names[k](v) if k in names else float(v)
     return np.array([p[k] for k in PARAM_NAMES], dtype=np.float64)
 
 

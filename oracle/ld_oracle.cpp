@@ -13,7 +13,11 @@
 // for:
 //   * the D3Q19 velocity set and weights (Qian, d'Humieres & Lallemand 1992);
 //   * BGK collision of f with the Guo-Zheng-Shi (2002) forcing term and the
-//     half-force velocity u = (j + F/2)/rho;
+//     half-force velocity u = (j + F/2)/rho; optionally (collision = 1) the
+//     two-relaxation-time form: the even and odd parts of each opposite pair,
+//     f+- = (f_i +- f_-i)/2 (and likewise feq and the Guo source), relax with
+//     omega+ = 1/tau_f and omega- = 1/tau-, tau- = 1/2 + Lambda/(tau_f - 1/2),
+//     the source parts scaled by (1 - omega+/2) and (1 - omega-/2);
 //   * BGK collision of g towards an equilibrium whose zeroth, first and second
 //     moments are phi, phi*u and Gamma*mu*I + phi*u*u;
 //   * the symmetric phi^4 free energy: mu = A phi + B phi^3 - kappa lap(phi),
@@ -73,6 +77,9 @@ double weight(int i) {
     return 1.0 / 36.0;
 }
 
+// Index of -c_i (odd i pairs with i + 1).
+int opposite(int i) { return i == 0 ? 0 : (i % 2 ? i + 1 : i - 1); }
+
 // ---------------------------------------------------------------------------
 // Dual number: value and one directional derivative (forward-mode AD).
 struct Dual {
@@ -105,6 +112,8 @@ struct Params {
     T A, B, kappa, Gamma, tau_f, tau_g, rho0;
     int stencil;  // 0: 7-point / central difference; 1: 19-point isotropic
     int force;    // 0: F = -phi grad(mu); 1: F = -div P (chemical stress)
+    int collision;  // 0: BGK; 1: two-relaxation-time with magic parameter lambda
+    T lambda;       // (tau_f - 1/2)(tau- - 1/2), collision = 1 only
 };
 
 struct Lattice {
@@ -144,6 +153,18 @@ void geq_site(T phi, const T u[3], T mu, T Gamma, T out[kQ]) {
         int c2 = kCx[i] * kCx[i] + kCy[i] * kCy[i] + kCz[i] * kCz[i];
         out[i] = weight(i) * (phi + 3.0 * phi * cu + 4.5 * pressure_dev * (double)(c2 - 1)
                               + 4.5 * phi * cu * cu - 1.5 * phi * uu);
+    }
+}
+
+// The Guo source without its prefactor: w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F.
+template <class T>
+void guo_bare_site(const T u[3], const T F[3], T out[kQ]) {
+    for (int i = 0; i < kQ; ++i) {
+        T cu = kCx[i] * u[0] + kCy[i] * u[1] + kCz[i] * u[2];
+        T ex = 3.0 * (kCx[i] - u[0]) + 9.0 * cu * kCx[i];
+        T ey = 3.0 * (kCy[i] - u[1]) + 9.0 * cu * kCy[i];
+        T ez = 3.0 * (kCz[i] - u[2]) + 9.0 * cu * kCz[i];
+        out[i] = weight(i) * (ex * F[0] + ey * F[1] + ez * F[2]);
     }
 }
 
@@ -355,9 +376,25 @@ void collide(const Lattice& L, const Params<T>& p, const Macro<T>& m, T* f, T* g
         T feq[kQ], src[kQ], geq[kQ];
         feq_site(m.rho[s], u, feq);
         guo_site(u, F, p.tau_f, src);
-        for (int i = 0; i < kQ; ++i) {
-            T fi = f[i * n + s];
-            f[i * n + s] = fi - (fi - feq[i]) / p.tau_f + src[i];
+        if (p.collision == 0) {
+            for (int i = 0; i < kQ; ++i) {
+                T fi = f[i * n + s];
+                f[i * n + s] = fi - (fi - feq[i]) / p.tau_f + src[i];
+            }
+        } else {
+            const T tau_m = 0.5 + p.lambda / (p.tau_f - 0.5);
+            const T pre_p = 1.0 - 1.0 / (2.0 * p.tau_f), pre_m = 1.0 - 1.0 / (2.0 * tau_m);
+            T bare[kQ], out[kQ];
+            guo_bare_site(u, F, bare);
+            for (int i = 0; i < kQ; ++i) {
+                const int o = opposite(i);
+                const T fi = f[i * n + s], fo = f[o * n + s];
+                const T fp = 0.5 * (fi + fo), fm = 0.5 * (fi - fo);
+                const T ep = 0.5 * (feq[i] + feq[o]), em = 0.5 * (feq[i] - feq[o]);
+                const T sp = 0.5 * (bare[i] + bare[o]), sm = 0.5 * (bare[i] - bare[o]);
+                out[i] = fi - (fp - ep) / p.tau_f - (fm - em) / tau_m + pre_p * sp + pre_m * sm;
+            }
+            for (int i = 0; i < kQ; ++i) f[i * n + s] = out[i];
         }
         geq_site(m.phi[s], u, m.mu[s], p.Gamma, geq);
         for (int i = 0; i < kQ; ++i) {
@@ -405,11 +442,11 @@ void init_state(const Lattice& L, const Params<T>& p, const T* phi, const T* rho
     }
 }
 
-// prm = {A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil, force}; the last
-// two are selectors (0 or 1).
+// prm = {A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil, force, collision,
+// lambda}; stencil, force and collision are selectors (0 or 1).
 Params<double> params_from(const double* prm) {
     return Params<double>{prm[0], prm[1], prm[2], prm[3], prm[4], prm[5], prm[6],
-                          prm[7] != 0.0 ? 1 : 0, prm[8] != 0.0 ? 1 : 0};
+                          prm[7] != 0.0 ? 1 : 0, prm[8] != 0.0 ? 1 : 0, prm[9] != 0.0 ? 1 : 0, prm[10]};
 }
 
 Params<Dual> dual_params_from(const double* prm, const double* dprm) {
@@ -423,6 +460,8 @@ Params<Dual> dual_params_from(const double* prm, const double* dprm) {
     p.rho0 = Dual(prm[6], dprm[6]);
     p.stencil = prm[7] != 0.0 ? 1 : 0;  // selectors, not differentiated
     p.force = prm[8] != 0.0 ? 1 : 0;
+    p.collision = prm[9] != 0.0 ? 1 : 0;
+    p.lambda = Dual(prm[10], 0.0);  // not differentiated
     return p;
 }
 
@@ -446,12 +485,12 @@ double plane_ordered_sum(const Lattice& L, const double* a) {
 
 // ---------------------------------------------------------------------------
 // C interface (called from Python through ctypes by the tests only).
-// prm = {A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil, force}; the
-// derivative direction dprm has the first seven. Return 0 on success, -1 on
-// bad arguments.
+// prm = {A, B, kappa, Gamma, tau_f, tau_g, rho0, stencil, force, collision,
+// lambda}; the derivative direction dprm has the first seven. Return 0 on
+// success, -1 on bad arguments.
 extern "C" {
 
-int orc_version() { return 3; }
+int orc_version() { return 4; }
 
 // Chemical stress P (6 x N, [xx, yy, zz, xy, xz, yz]) of a phi field with the
 // stencils and parameters of prm.

@@ -273,8 +273,8 @@ def _project(field, k_index, axis_len):
     return 2.0 / axis_len * float((field * np.sin(2 * math.pi * k_index * x / axis_len)).sum())
 
 
-def _shear_rate(orc, ny, tau_f, t0=100, t1=1000):
-    prm = orc.param_vector(tau_f=tau_f)
+def _shear_rate(orc, ny, tau_f, t0=100, t1=1000, prm=None):
+    prm = orc.param_vector(tau_f=tau_f) if prm is None else prm
     nx = nz = 1
     u = inputs.shear_wave_u(nx, ny, nz, 1e-3)
     phi = np.zeros((nz, ny, nx))
@@ -621,7 +621,82 @@ def test_tangent_linear_with_stress_force(orc):
     phi0 = inputs.spinodal_phi(nx, ny, nz, seed=21, amplitude=0.3)
     target = inputs.spinodal_phi(nx, ny, nz, seed=22, amplitude=0.3)
     dphi = np.random.default_rng(6).standard_normal(phi0.shape)
-    dprm = np.zeros(9)
+    dprm = np.zeros(len(prm))
+    dprm[2], dprm[4] = 0.3, -0.7
+    steps = 6
+    _, dL = orc.loss_jvp(phi0, target, prm, steps, dphi0=dphi, dprm=dprm)
+    h = 1e-5
+    fd = (orc.loss(phi0 + h * dphi, target, prm + h * dprm, steps) -
+          orc.loss(phi0 - h * dphi, target, prm - h * dprm, steps)) / (2 * h)
+    assert dL == pytest.approx(fd, rel=1e-7)
+
+
+# --------------------------------------------------------------------------
+# Two-relaxation-time collision of f (catches a wrong even/odd split of f,
+# feq or the Guo source, a wrong prefactor on either part, a tau- that moves
+# the shear viscosity, and any loss of mass or momentum).
+
+
+def test_trt_with_equal_rates_is_bgk(orc):
+    """Lambda = (tau - 1/2)^2 makes tau- = tau+: the two-rate collision is
+    the one-rate one, to rounding."""
+    tau = 0.8
+    bgk = orc.param_vector(tau_f=tau)
+    trt = orc.param_vector(tau_f=tau, collision="trt", magic=(tau - 0.5) ** 2)
+    phi = inputs.spinodal_phi(6, 5, 4, seed=12, amplitude=0.5)
+    rng = np.random.default_rng(2)
+    u = 0.05 * rng.standard_normal((3,) + phi.shape)
+    fa, ga = orc.step(*orc.init(phi, bgk, u=u), bgk, 10)
+    fb, gb = orc.step(*orc.init(phi, trt, u=u), trt, 10)
+    assert np.abs(fa - fb).max() < 1e-14
+    assert np.abs(ga - gb).max() < 1e-15
+
+
+@pytest.mark.parametrize("magic", [0.1875, 0.25, 1.0])
+def test_trt_shear_viscosity_depends_on_tau_plus_only(orc, magic):
+    """The shear wave decays at nu k^2 with nu = (tau_f - 1/2)/3 whatever the
+    odd-part rate (the magic parameter moves only higher-order terms)."""
+    tau, ny = 0.7, 64
+    k = 2 * math.pi / ny
+    nu = (tau - 0.5) / 3.0
+    prm = orc.param_vector(tau_f=tau, collision="trt", magic=magic)
+    rate = _shear_rate(orc, ny, tau, prm=prm)
+    assert abs(rate / (nu * k * k) - 1.0) < 0.01
+
+
+def test_trt_conserves_mass_and_adds_the_force(orc):
+    prm = orc.param_vector(tau_f=0.9, collision="trt", magic=0.25, kappa=0.06)
+    phi = inputs.spinodal_phi(7, 6, 5, seed=14, amplitude=0.5)
+    f, g = orc.init(phi, prm)
+    m = orc.macros(f, g, prm)
+    t0 = m["totals"].copy()
+    force = m["force"].reshape(3, -1).sum(1)
+    f1, g1 = orc.step(f, g, prm, 1)
+    t1 = orc.macros(f1, g1, prm)["totals"]
+    assert abs(t1[0] - t0[0]) < 1e-13 * phi.size
+    assert abs(t1[1] - t0[1]) < 1e-13 * phi.size
+    assert np.abs((t1[2:] - t0[2:]) - force).max() < 1e-14
+
+
+def test_trt_uniform_equilibrium_is_fixed_point(orc):
+    prm = orc.param_vector(tau_f=0.7, collision="trt", magic=0.1875)
+    phi = np.full((4, 4, 4), 0.3)
+    u = np.zeros((3, 4, 4, 4))
+    u[0], u[2] = 0.02, -0.01
+    f, g = orc.init(phi, prm, u=u)
+    f1, g1 = orc.step(f, g, prm, 1)
+    eps = np.finfo(np.float64).eps
+    assert np.abs(f1 - f).max() <= 4 * eps * np.abs(f).max()
+    assert np.abs(g1 - g).max() <= 4 * eps * np.abs(g).max()
+
+
+def test_tangent_linear_with_trt(orc):
+    nz, ny, nx = 5, 6, 4
+    prm = orc.param_vector(tau_f=0.9, collision="trt", magic=0.25)
+    phi0 = inputs.spinodal_phi(nx, ny, nz, seed=21, amplitude=0.3)
+    target = inputs.spinodal_phi(nx, ny, nz, seed=22, amplitude=0.3)
+    dphi = np.random.default_rng(6).standard_normal(phi0.shape)
+    dprm = np.zeros(len(prm))
     dprm[2], dprm[4] = 0.3, -0.7
     steps = 6
     _, dL = orc.loss_jvp(phi0, target, prm, steps, dphi0=dphi, dprm=dprm)
