@@ -88,6 +88,18 @@ enum { LD_STENCIL_7 = 0, LD_STENCIL_19 = 1 };
  *   Fixed at ld_create (its 6 stress fields are part of the workspace). */
 enum { LD_FORCE_POTENTIAL = 0, LD_FORCE_STRESS = 1 };
 
+/* Collision of f (the "Collision" kernel of Sec. 2.1.1; the paper gives no
+ * formula).
+ * LD_COLLISION_BGK: one relaxation time tau_f, Guo forcing (default).
+ * LD_COLLISION_TRT: two relaxation times. The even and odd parts of each
+ *   opposite pair, f+- = (f_i +- f_-i)/2, and likewise of f^eq and of the Guo
+ *   source, relax with omega+ = 1/tau_f and omega- = 1/tau-, where
+ *   tau- = 1/2 + magic/(tau_f - 1/2); the source parts carry (1 - omega+/2)
+ *   and (1 - omega-/2). The shear viscosity is still (tau_f - 1/2)/3.
+ *   GENERIC kernel only (AUTO picks it; FUSED and FUSED_TMA give LD_EINVAL);
+ *   no adjoint. Fixed at ld_create. */
+enum { LD_COLLISION_BGK = 0, LD_COLLISION_TRT = 1 };
+
 enum {
     LD_OK = 0,
     LD_EINVAL = -1,     /* bad argument: dims < 4, null/host pointer, tau <= 1/2, small workspace */
@@ -104,6 +116,8 @@ typedef struct {
     int kernel;                /* LD_KERNEL_AUTO / GENERIC / FUSED / FUSED_TMA */
     int stencil;               /* LD_STENCIL_7 / LD_STENCIL_19 */
     int force;                 /* LD_FORCE_POTENTIAL / LD_FORCE_STRESS */
+    int collision;             /* LD_COLLISION_BGK / LD_COLLISION_TRT */
+    double magic;              /* TRT: (tau_f - 1/2)(tau- - 1/2) > 0 (3/16 is usual) */
 } ld_params;
 
 typedef struct ld_ctx ld_ctx;

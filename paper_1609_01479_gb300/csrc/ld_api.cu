@@ -89,6 +89,12 @@ bool params_ok(const ld_params* p, const char** why) {
     if (p->force != LD_FORCE_POTENTIAL && p->force != LD_FORCE_STRESS) return *why = "unknown force form", false;
     if (p->force == LD_FORCE_STRESS && (p->kernel == LD_KERNEL_FUSED || p->kernel == LD_KERNEL_FUSED_TMA))
         return *why = "the stress form of the force runs on the generic kernel only", false;
+    if (p->collision != LD_COLLISION_BGK && p->collision != LD_COLLISION_TRT) return *why = "unknown collision", false;
+    if (p->collision == LD_COLLISION_TRT) {
+        if (!(p->magic > 0.0) || !isfinite(p->magic)) return *why = "the TRT magic parameter must be positive", false;
+        if (p->kernel == LD_KERNEL_FUSED || p->kernel == LD_KERNEL_FUSED_TMA)
+            return *why = "the TRT collision runs on the generic kernel only", false;
+    }
     return true;
 }
 
@@ -153,8 +159,8 @@ int ld_create(int nx, int ny, int nz, const ld_params* p, void* dev_workspace, s
     if ((uintptr_t)dev_workspace % kAlign) return fail(nullptr, LD_EINVAL, "workspace must be 256-byte aligned");
     if (bytes < L.total)
         return fail(nullptr, LD_EINVAL, "workspace of %zu bytes is smaller than the %zu needed", bytes, L.total);
-    // the stress form of the force runs on the generic kernel
-    const int step_kernel = p->force == LD_FORCE_STRESS
+    // the stress form of the force and the TRT collision run on the generic kernel
+    const int step_kernel = p->force == LD_FORCE_STRESS || p->collision == LD_COLLISION_TRT
                                 ? ld::kStepGeneric
                                 : ld::choose_step_kernel(nx, ny, nz, p->precision, p->kernel);
     if (step_kernel == 0)
@@ -224,8 +230,8 @@ int ld_set_params(ld_ctx* c, const ld_params* p) {
     if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
     if (!params_ok(p, &why)) return fail(c, LD_EINVAL, "%s", why);
     if (p->precision != c->prm.precision || p->kernel != c->prm.kernel || p->rho0 != c->prm.rho0 ||
-        p->force != c->prm.force)
-        return fail(c, LD_EINVAL, "precision, kernel, rho0 and the force form are fixed at ld_create");
+        p->force != c->prm.force || p->collision != c->prm.collision)
+        return fail(c, LD_EINVAL, "precision, kernel, rho0, the force form and the collision are fixed at ld_create");
     c->prm = *p;
     return LD_OK;
 }
@@ -379,13 +385,14 @@ int check_adj(ld_ctx* c) {
 extern "C" {
 
 size_t ld_adjoint_workspace_bytes(const ld_ctx* c) {
-    return c && c->prm.force == LD_FORCE_POTENTIAL ? adj_layout_of(c).total : 0;
+    return c && c->prm.force == LD_FORCE_POTENTIAL && c->prm.collision == LD_COLLISION_BGK ? adj_layout_of(c).total
+                                                                                            : 0;
 }
 
 int ld_adjoint_attach(ld_ctx* c, void* dev_workspace, size_t bytes) {
     if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
-    if (c->prm.force != LD_FORCE_POTENTIAL)
-        return fail(c, LD_EINVAL, "the adjoint is built for the force F = -phi grad(mu) only");
+    if (c->prm.force != LD_FORCE_POTENTIAL || c->prm.collision != LD_COLLISION_BGK)
+        return fail(c, LD_EINVAL, "the adjoint is built for the BGK collision with F = -phi grad(mu) only");
     const AdjLayout L = adj_layout_of(c);
     if (!is_device_ptr(dev_workspace)) return fail(c, LD_EINVAL, "adjoint workspace is not a device pointer");
     if ((uintptr_t)dev_workspace % kAlign) return fail(c, LD_EINVAL, "adjoint workspace must be 256-byte aligned");

@@ -92,6 +92,9 @@ struct Model {
     R omega_f, omega_g;  // 1/tau
     R force_pre;         // 1 - 1/(2 tau_f)
     int iso;             // 1: 19-point isotropic stencils (LD_STENCIL_19)
+    int trt;             // 1: two-relaxation-time collision of f (LD_COLLISION_TRT)
+    R omega_m;           // TRT: 1/tau- of the odd parts
+    R force_pre_m;       // TRT: 1 - 1/(2 tau-)
 };
 
 // Model constants from the C-ABI parameters.
@@ -106,6 +109,10 @@ inline Model<R> model_of(const ld_params& p) {
     m.omega_g = (R)(1.0 / p.tau_g);
     m.force_pre = (R)(1.0 - 0.5 / p.tau_f);
     m.iso = p.stencil == LD_STENCIL_19 ? 1 : 0;
+    m.trt = p.collision == LD_COLLISION_TRT ? 1 : 0;
+    const double tau_m = m.trt ? 0.5 + p.magic / (p.tau_f - 0.5) : p.tau_f;
+    m.omega_m = (R)(1.0 / tau_m);
+    m.force_pre_m = (R)(1.0 - 0.5 / tau_m);
     return m;
 }
 
@@ -283,6 +290,42 @@ __device__ __forceinline__ void collide_f<float>(float (&f)[Q], float rho, float
     const float feq0 = rho - 2.0f * moving;
     const float src0 = m.force_pre * wgt<float>(0) * (-3.0f * uF);
     f[0] = keep * f[0] + (m.omega_f * feq0 + src0);
+}
+
+// Two-relaxation-time collision of f in place (LD_COLLISION_TRT). Each
+// opposite pair (i, i+1), c_{i+1} = -c_i, splits into even and odd parts:
+//   f+- = (f_i +- f_{i+1})/2,  feq+ = w rho (1 - 3/2 u.u + 9/2 (c.u)^2), feq- = 3 w rho c.u,
+//   S+ = w (9 (c.u)(c.F) - 3 u.F),  S- = 3 w c.F   (the Guo source without prefactor),
+//   new+ = f+ - omega+ (f+ - feq+) + (1 - omega+/2) S+,
+//   new- = f- - omega- (f- - feq-) + (1 - omega-/2) S-,
+//   f_i = new+ + new-,  f_{i+1} = new+ - new-.
+// The rest population has only an even part. In FP32 its equilibrium is rho
+// minus the 18 moving ones (as in collide_f), which keeps mass exact.
+template <class R>
+__device__ __forceinline__ void collide_f_trt(R (&f)[Q], R rho, R ux, R uy, R uz, R Fx, R Fy, R Fz,
+                                              const Model<R>& m) {
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R uF = ux * Fx + uy * Fy + uz * Fz;
+    R moving = R(0);
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const R w = wgt<R>(i);
+        const R cu = cdot(i, ux, uy, uz);
+        const R cF = cdot(i, Fx, Fy, Fz);
+        const R ep = w * rho * (R(1) + R(4.5) * cu * cu - R(1.5) * uu);
+        const R em = R(3) * w * rho * cu;
+        const R sp = w * (R(9) * cu * cF - R(3) * uF);
+        const R sm = R(3) * w * cF;
+        const R fp = R(0.5) * (f[i] + f[i + 1]), fm = R(0.5) * (f[i] - f[i + 1]);
+        const R np = fp - m.omega_f * (fp - ep) + m.force_pre * sp;
+        const R nm = fm - m.omega_m * (fm - em) + m.force_pre_m * sm;
+        f[i] = np + nm;
+        f[i + 1] = np - nm;
+        moving += ep;
+    }
+    const R feq0 = sizeof(R) == 4 ? rho - R(2) * moving : wgt<R>(0) * rho * (R(1) - R(1.5) * uu);
+    const R s0 = wgt<R>(0) * (R(3) * (-uF));
+    f[0] = f[0] - m.omega_f * (f[0] - feq0) + m.force_pre * s0;
 }
 
 // BGK collision of g in place; FP64 direction by direction, FP32 on opposite

@@ -229,7 +229,10 @@ __global__ void __launch_bounds__(kRowThreads, rows_blocks_per_sm<P>())
     }
     R ux, uy, uz;
     guo_velocity(rho, jx, jy, jz, Fx, Fy, Fz, ux, uy, uz);
-    collide_f(f, rho, ux, uy, uz, Fx, Fy, Fz, m);
+    if (m.trt)
+        collide_f_trt(f, rho, ux, uy, uz, Fx, Fy, Fz, m);
+    else
+        collide_f(f, rho, ux, uy, uz, Fx, Fy, Fz, m);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int d = s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +

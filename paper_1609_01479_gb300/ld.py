@@ -31,6 +31,8 @@ LD_STENCIL_7, LD_STENCIL_19 = 0, 1
 STENCILS = {7: LD_STENCIL_7, 19: LD_STENCIL_19}
 LD_FORCE_POTENTIAL, LD_FORCE_STRESS = 0, 1
 FORCES = {"potential": LD_FORCE_POTENTIAL, "stress": LD_FORCE_STRESS}
+LD_COLLISION_BGK, LD_COLLISION_TRT = 0, 1
+COLLISIONS = {"bgk": LD_COLLISION_BGK, "trt": LD_COLLISION_TRT}
 Q = 19
 
 
@@ -38,7 +40,8 @@ class LdParams(ctypes.Structure):
     _fields_ = [("A", ctypes.c_double), ("B", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("Gamma", ctypes.c_double), ("tau_f", ctypes.c_double), ("tau_g", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("stencil", ctypes.c_int), ("force", ctypes.c_int)]
+                ("stencil", ctypes.c_int), ("force", ctypes.c_int), ("collision", ctypes.c_int),
+                ("magic", ctypes.c_double)]
 
 
 class LdError(RuntimeError):
@@ -121,14 +124,17 @@ def _call(name, ctx, *args):
 
 
 def make_params(A=-0.0625, B=0.0625, kappa=0.04, Gamma=0.5, tau_f=1.0, tau_g=1.0, rho0=1.0,
-                precision="fp32", kernel="auto", stencil=7, force="potential") -> LdParams:
+                precision="fp32", kernel="auto", stencil=7, force="potential", collision="bgk",
+                magic=0.1875) -> LdParams:
     """ld_params; stencil is 7 (7-point Laplacian, central difference) or 19
     (the 19-point isotropic forms); force is "potential" (-phi grad mu) or
-    "stress" (-div P)."""
+    "stress" (-div P); collision is "bgk" or "trt" (with the magic parameter
+    (tau_f - 1/2)(tau- - 1/2))."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     kern = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
     frc = FORCES[force] if isinstance(force, str) else int(force)
-    return LdParams(A, B, kappa, Gamma, tau_f, tau_g, rho0, prec, kern, STENCILS[int(stencil)], frc)
+    col = COLLISIONS[collision] if isinstance(collision, str) else int(collision)
+    return LdParams(A, B, kappa, Gamma, tau_f, tau_g, rho0, prec, kern, STENCILS[int(stencil)], frc, col, magic)
 
 
 # ---------------------------------------------------------------------------
@@ -295,6 +301,8 @@ class LdSim:
             model = dict(model, stencil=STENCILS[int(model["stencil"])])
         if isinstance(model.get("force"), str):
             model = dict(model, force=FORCES[model["force"]])
+        if isinstance(model.get("collision"), str):
+            model = dict(model, collision=COLLISIONS[model["collision"]])
         kw.update(model)
         self.params = LdParams(*[kw[f[0]] for f in LdParams._fields_])
         ld_set_params(self.ctx, self.params)

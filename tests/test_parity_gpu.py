@@ -42,6 +42,8 @@ def gpu_run(ld, phi, steps, precision="fp64", kernel="auto", prm=None, rho=None,
         model["stencil"] = 19 if model["stencil"] else 7
     if "force" in model:
         model["force"] = "stress" if model["force"] else "potential"
+    if "collision" in model:
+        model["collision"] = "trt" if model["collision"] else "bgk"
     sim = ld.LdSim(nx, ny, nz, precision=precision, kernel=kernel, **model)
     sim.init(torch.from_numpy(phi).cuda(),
              None if rho is None else torch.from_numpy(rho).cuda(),
@@ -198,6 +200,46 @@ def test_stress_force_refusals(ld):
     assert e.value.code == ld.LD_EINVAL
     with pytest.raises(ld.LdError):
         sim.set_params(force="potential")
+    sim.close()
+
+
+@pytest.mark.parametrize("shape", [(7, 6, 5), (5, 9, 33), (8, 8, 32)])
+@pytest.mark.parametrize("magic", [0.1875, 1.0])
+def test_fp64_trt_collision(ld, shape, magic):
+    """The two-relaxation-time collision (LD_COLLISION_TRT) on the generic
+    launches: 1e-12 against the oracle, with nonzero flow and density so that
+    every even and odd part is exercised."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng(29)
+    phi = inputs.spinodal_phi(nx, ny, nz, seed=29, amplitude=0.4)
+    rho = 1.0 + 0.02 * rng.standard_normal((nz, ny, nx))
+    u = 0.03 * rng.standard_normal((3, nz, ny, nx))
+    prm = oracle.param_vector(tau_f=0.8, tau_g=1.1, collision="trt", magic=magic)
+    assert_parity(gpu_run(ld, phi, 20, prm=prm, rho=rho, u=u), oracle_run(phi, 20, prm=prm, rho=rho, u=u), FP64_TOL)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16dev", 1e-2)])
+def test_reduced_precision_trt(ld, precision, tol):
+    nz, ny, nx = 32, 32, 32
+    phi = inputs.spinodal_phi(nx, ny, nz, seed=2)
+    prm = oracle.param_vector(collision="trt", tau_f=0.8)
+    g = gpu_run(ld, phi, 100, precision=precision, prm=prm)
+    r = oracle_run(phi, 100, prm=prm)
+    assert rel_l2(g["phi"], r["phi"]) <= tol
+    assert rel_l2(g["rho"], r["rho"]) <= tol
+
+
+def test_trt_refusals(ld):
+    for kernel in ("fused", "fused_tma"):
+        with pytest.raises(ld.LdError) as e:
+            ld.LdSim(32, 8, 4, precision="fp32", kernel=kernel, collision="trt")
+        assert e.value.code == ld.LD_EINVAL
+    with pytest.raises(ld.LdError):
+        ld.LdSim(8, 8, 8, precision="fp32", collision="trt", magic=0.0)
+    sim = ld.LdSim(8, 8, 8, precision="fp32", collision="trt")
+    assert ld.ld_adjoint_workspace_bytes(sim.ctx) == 0
+    with pytest.raises(ld.LdError):
+        sim.set_params(collision="bgk")
     sim.close()
 
 
