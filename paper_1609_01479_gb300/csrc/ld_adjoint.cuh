@@ -57,7 +57,7 @@ constexpr int adj_ctas_per_sm() {
 }
 
 // Step 1 + 2: local adjoint at every site.
-template <int P>
+template <int P, bool ISO>
 __global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<P>())
     k_adj_local(Geom g, Model<typename Prec<P>::real_t> m, const typename Prec<P>::store_t* __restrict__ tf,
                 const typename Prec<P>::real_t* __restrict__ phi, const typename Prec<P>::real_t* __restrict__ mu,
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<P>())
         // forward quantities
         const R ph = phi[s];
         R gmx, gmy, gmz;
-        if (m.iso) {
+        if constexpr (ISO) {
             auto nb = [&](int i) {
                 return mu[site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny), step_coord(z, cz(i), g.nz))];
             };
@@ -172,9 +172,9 @@ __global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<P>())
 // Step 3: mubar += transpose of the gradient applied to gmbar; kappa
 // partials mubar (-lap phi). 7-point: the transposed central difference;
 // 19-point: mubar(y) += sum_i 3 w_i c_i . gmbar(y - c_i).
-template <class R>
+template <class R, bool ISO>
 __global__ void __launch_bounds__(kAdjThreads)
-    k_adj_mu(Geom g, int iso, const R* __restrict__ phi, const R* __restrict__ gmb, R* __restrict__ mub,
+    k_adj_mu(Geom g, const R* __restrict__ phi, const R* __restrict__ gmb, R* __restrict__ mub,
              double* __restrict__ part) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double kappa_bar = 0.0;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kAdjThreads)
         int x, y, z;
         site_coords(g, s, x, y, z);
         R t, lap;
-        if (iso) {
+        if constexpr (ISO) {
             t = mub[s];
             lap = R(0);
 #pragma unroll
@@ -211,9 +211,9 @@ __global__ void __launch_bounds__(kAdjThreads)
 
 // Laplacian (7-point or 19-point, symmetric: its own transpose) of a field
 // at site s = (x, y, z), in the type of the field.
-template <class T>
-__device__ __forceinline__ T lap_at(const Geom& g, int iso, const T* h, long long s, int x, int y, int z) {
-    if (iso) {
+template <bool ISO, class T>
+__device__ __forceinline__ T lap_at(const Geom& g, const T* h, long long s, int x, int y, int z) {
+    if constexpr (ISO) {
         T lap = T(0);
 #pragma unroll
         for (int i = 1; i < Q; ++i)
@@ -228,7 +228,7 @@ __device__ __forceinline__ T lap_at(const Geom& g, int iso, const T* h, long lon
 }
 
 // Step 4: phibar, the per-site part P of gbar at t.
-template <class R>
+template <class R, bool ISO>
 __global__ void __launch_bounds__(kAdjThreads)
     k_adj_p(Geom g, Model<R> m, const R* __restrict__ phi, const R* __restrict__ mub, const R* __restrict__ phib,
             R* __restrict__ pb0) {
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kAdjThreads)
     int x, y, z;
     site_coords(g, s, x, y, z);
     const R ph = phi[s];
-    const R lapm = lap_at(g, m.iso, mub, s, x, y, z);
+    const R lapm = lap_at<ISO>(g, mub, s, x, y, z);
     pb0[s] = phib[s] + (m.A + R(3) * m.B * ph * ph) * mub[s] - m.kappa * lapm;
 }
 
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kAdjThreads)
 // Initialiser adjoint, part 2: dL/dphi0 and the kappa partials
 // (g = geq(phi0, u0, mu(phi0)); f does not depend on phi0, kappa or tau_f).
 // Per-site sums in the arithmetic type; outputs and partials in FP64.
-template <class R>
+template <class R, bool ISO>
 __global__ void __launch_bounds__(kAdjThreads)
     k_adj_init_phi(Geom g, Model<R> m, const double* __restrict__ phi0, const double* __restrict__ u0,
                    const R* __restrict__ gb, const R* __restrict__ pb, const R* __restrict__ mub,
@@ -331,9 +331,9 @@ __global__ void __launch_bounds__(kAdjThreads)
         }
         const R ph = (R)phi0[s];
         const R mb = mub[s];
-        const R lapm = lap_at(g, m.iso, mub, s, x, y, z);
+        const R lapm = lap_at<ISO>(g, mub, s, x, y, z);
         grad_phi0[s] = (double)(acc + (m.A + R(3) * m.B * ph * ph) * mb - m.kappa * lapm);
-        const double lap = lap_at(g, m.iso, phi0, s, x, y, z);
+        const double lap = lap_at<ISO>(g, phi0, s, x, y, z);
         kappa_bar = -(double)mb * lap;
     }
     if (threadIdx.x == 0) part[2 * (long long)blockIdx.x] = 0.0;  // no tau_f term in the initialiser
@@ -384,8 +384,8 @@ AdjPtrs<P> adj_ptrs(ld_ctx* c, int in_buf) {
     return p;
 }
 
-template <int P>
-cudaError_t adj_step_p(ld_ctx* c, const void* state_t, const void* fields_t, double* grad) {
+template <int P, bool ISO>
+cudaError_t adj_step_iso(ld_ctx* c, const void* state_t, const void* fields_t, double* grad) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     const Geom g = to_dev(c->geom);
@@ -398,14 +398,20 @@ cudaError_t adj_step_p(ld_ctx* c, const void* state_t, const void* fields_t, dou
     const AdjPtrs<P> p = adj_ptrs<P>(c, c->adj_cur);
     const Model<R> m = model_of<R>(c->prm);
     const unsigned nb = blocks_for(g.n);
-    k_adj_local<P><<<nb, kAdjThreads, 0, c->stream>>>(g, m, (const S*)f_part(c, state_t), phi, mu, c->ref, p.fb1,
+    k_adj_local<P, ISO><<<nb, kAdjThreads, 0, c->stream>>>(g, m, (const S*)f_part(c, state_t), phi, mu, c->ref, p.fb1,
                                                       p.gb1, p.pb1, p.fb0, p.gb0, p.gmb, p.mub, p.phib, c->adj_part);
-    k_adj_mu<R><<<nb, kAdjThreads, 0, c->stream>>>(g, m.iso, phi, p.gmb, p.mub, c->adj_part);
-    k_adj_p<R><<<nb, kAdjThreads, 0, c->stream>>>(g, m, phi, p.mub, p.phib, p.pb0);
+    k_adj_mu<R, ISO><<<nb, kAdjThreads, 0, c->stream>>>(g, phi, p.gmb, p.mub, c->adj_part);
+    k_adj_p<R, ISO><<<nb, kAdjThreads, 0, c->stream>>>(g, m, phi, p.mub, p.phib, p.pb0);
     if (grad)
         k_adj_finalize<<<1, kAdjThreads, 0, c->stream>>>(c->adj_part, nb, -1.0 / (c->prm.tau_f * c->prm.tau_f),
                                                          grad);
     return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t adj_step_p(ld_ctx* c, const void* state_t, const void* fields_t, double* grad) {
+    return c->prm.stencil == LD_STENCIL_19 ? adj_step_iso<P, true>(c, state_t, fields_t, grad)
+                                           : adj_step_iso<P, false>(c, state_t, fields_t, grad);
 }
 
 template <int P>
@@ -417,17 +423,23 @@ cudaError_t adj_seed_p(ld_ctx* c, const double* phibar) {
     return cudaGetLastError();
 }
 
-template <int P>
-cudaError_t adj_init_p(ld_ctx* c, const double* phi0, const double* u0, double* grad_phi0, double* grad) {
+template <int P, bool ISO>
+cudaError_t adj_init_iso(ld_ctx* c, const double* phi0, const double* u0, double* grad_phi0, double* grad) {
     using R = typename Prec<P>::real_t;
     const Geom g = to_dev(c->geom);
     const AdjPtrs<P> p = adj_ptrs<P>(c, c->adj_cur);
     const unsigned nb = blocks_for(g.n);
     k_adj_init_mu<R><<<nb, kAdjThreads, 0, c->stream>>>(g, (R)c->prm.Gamma, p.gb1, p.pb1, p.mub);
-    k_adj_init_phi<R><<<nb, kAdjThreads, 0, c->stream>>>(g, model_of<R>(c->prm), phi0, u0, p.gb1, p.pb1, p.mub,
+    k_adj_init_phi<R, ISO><<<nb, kAdjThreads, 0, c->stream>>>(g, model_of<R>(c->prm), phi0, u0, p.gb1, p.pb1, p.mub,
                                                          grad_phi0, c->adj_part);
     if (grad) k_adj_finalize<<<1, kAdjThreads, 0, c->stream>>>(c->adj_part, nb, 0.0, grad);
     return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t adj_init_p(ld_ctx* c, const double* phi0, const double* u0, double* grad_phi0, double* grad) {
+    return c->prm.stencil == LD_STENCIL_19 ? adj_init_iso<P, true>(c, phi0, u0, grad_phi0, grad)
+                                           : adj_init_iso<P, false>(c, phi0, u0, grad_phi0, grad);
 }
 
 template <int P>
