@@ -7,8 +7,8 @@
  * "Collision" and "Propagation"), in its binary-fluid form:
  *
  *   rho = sum_i f_i,  j = sum_i f_i c_i,  phi = sum_i g_i      (moments)
- *   mu  = A phi + B phi^3 - kappa lap(phi)       (7-point Laplacian)
- *   F   = -phi grad(mu)                           (2-point central difference)
+ *   mu  = A phi + B phi^3 - kappa lap(phi)       (7-point Laplacian by default)
+ *   F   = -phi grad(mu)                           (2-point central difference by default)
  *   u   = (j + F/2) / rho                         (Guo, Zheng & Shi 2002)
  *   f*_i = f_i - (f_i - feq_i(rho,u))/tau_f + (1 - 1/(2 tau_f)) w_i [3(c_i-u) + 9(c_i.u)c_i].F
  *   g*_i = g_i - (g_i - geq_i(phi,u,mu))/tau_g
@@ -20,6 +20,10 @@
  * on a periodic nx*ny*nz lattice, D3Q19 velocity set in the order: rest,
  * +x,-x,+y,-y,+z,-z, then the face diagonals in (v,-v) pairs
  * (++0,--0,+-0,-+0, +0+,-0-,+0-,-0+, 0++,0--,0+-,0-+).
+ * The lines above are the default step; ld_params selects 19-point
+ * stencils (LD_STENCIL_19), the force -div P (LD_FORCE_STRESS) and a
+ * two-relaxation-time collision of f (LD_COLLISION_TRT), described with
+ * their enums below.
  *
  * Conventions shared by every call:
  *   - Site order s = x + nx*(y + ny*z), x fastest. Scalar fields are double[N],
@@ -139,12 +143,13 @@ int ld_destroy(ld_ctx* ctx);
 /* Change the stream later calls are ordered on. */
 int ld_set_stream(ld_ctx* ctx, void* cuda_stream);
 
-/* Replace A, B, kappa, Gamma, tau_f, tau_g (precision, kernel and rho0 must
- * stay as created). Takes effect at the next launch. */
+/* Replace A, B, kappa, Gamma, tau_f, tau_g, the stencil and magic (precision,
+ * kernel, rho0, force and collision must stay as created: LD_EINVAL
+ * otherwise). Takes effect at the next launch. */
 int ld_set_params(ld_ctx* ctx, const ld_params* p);
 
 /* Initial state (equilibrium, no force): f = feq(rho, u), g = geq(phi, u, mu(phi))
- * with mu from the 7-point Laplacian of phi. phi: device double[N];
+ * with mu from the selected stencil's Laplacian of phi. phi: device double[N];
  * rho: device double[N] or NULL (rho0 everywhere); u: device double[3][N] or
  * NULL (at rest). Also fixes the deviation reference of LD_FP16DEV/LD_BF16DEV. */
 int ld_init(ld_ctx* ctx, const double* phi, const double* rho, const double* u);
@@ -154,8 +159,8 @@ int ld_init(ld_ctx* ctx, const double* phi, const double* rho, const double* u);
 int ld_step(ld_ctx* ctx, int nsteps);
 
 /* Macroscopic fields of the current (pre-collision) state. Each output may be
- * NULL. rho, phi: double[N]; u = (j + F/2)/rho: double[3][N];
- * grad_phi (central difference): double[3][N]; totals: double[5] =
+ * NULL. rho, phi: double[N]; u = (j + F/2)/rho with the selected force:
+ * double[3][N]; grad_phi (the selected stencil's gradient): double[3][N]; totals: double[5] =
  * {sum rho, sum phi, sum jx, sum jy, sum jz}, each summed in FP64 in a fixed
  * order (bitwise reproducible run to run). Asynchronous. */
 int ld_moments(ld_ctx* ctx, double* rho, double* u, double* phi, double* grad_phi, double* totals);
@@ -205,8 +210,9 @@ int ld_step_between(ld_ctx* ctx, const void* src_state, void* dst_state, void* f
  * linearised step equations at the top of this file:
  *   reverse propagation fbar*_i(x) = fbar_i(x + c_i) (and g), then the adjoint
  *   of both collisions and of u = (j+F/2)/rho and F = -phi grad(mu), whose
- *   non-local parts are the transposed central difference and the (symmetric)
- *   7-point Laplacian; gbar_i = (1 - 1/tau_g) gbar*_i + phibar.
+ *   non-local parts are the transposed gradient and the (symmetric)
+ *   Laplacian of the selected stencil; gbar_i = (1 - 1/tau_g) gbar*_i + phibar.
+ * Defined for LD_FORCE_POTENTIAL with LD_COLLISION_BGK only.
  * The adjoint state is held in the arithmetic type (FP64 for LD_FP64,
  * FP32 otherwise); parameter sums are FP64 in a fixed order. */
 

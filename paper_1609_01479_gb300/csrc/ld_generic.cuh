@@ -1,6 +1,7 @@
 // Generic kernels: any lattice size >= 4 in every dimension, one thread per
-// site. The step runs as three launches in site order -- phi (zeroth moment
-// of g), mu (7-point stencil), and collide+propagate -- and the same file holds the
+// site. The step runs as three launches in row order -- phi (zeroth moment
+// of g), mu (7- or 19-point Laplacian), and collide+propagate, with a fourth
+// for the chemical stress when the force is -div P -- and the same file holds the
 // initialiser, the macroscopic output, the FP64 conservation sums, the
 // codec I/O and propagation alone. Templates only: instantiated per storage
 // precision by ld_prec_f64.cu and ld_prec_lp.cu.
@@ -74,7 +75,8 @@ __global__ void __launch_bounds__(kRowThreads) k_phi(RowGeom rg, I npad, const t
     phi[s] = acc;
 }
 
-// Stage 2: mu = A phi + B phi^3 - kappa lap(phi), 7-point Laplacian.
+// Stage 2: mu = A phi + B phi^3 - kappa lap(phi), with the 7-point or the
+// 19-point Laplacian.
 template <class R>
 __global__ void __launch_bounds__(kRowThreads) k_mu(RowGeom rg, Model<R> m, const R* __restrict__ phi,
                                                     R* __restrict__ mu) {
