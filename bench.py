@@ -24,6 +24,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -79,21 +80,30 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+_TOKENS = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\\n])*"|\'(?:\\.|[^\'\\\n])*\'', re.S)
+
+
+def _code_hash(rels):
+    """Hash of the code in the given sources with comments removed and
+    whitespace runs collapsed, so that a record taken on a kernel stays
+    valid through edits of its comments but not of its code."""
     h = hashlib.sha256()
-    for rel in ("paper_1609_01479_gb300/csrc/ld_fused.cuh", "paper_1609_01479_gb300/csrc/ld_common.cuh"):
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(fh.read())
+    for rel in rels:
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as fh:
+            text = fh.read()
+        code = _TOKENS.sub(lambda mt: " " if mt.group(0)[0] == "/" else mt.group(0), text)
+        h.update(" ".join(code.split()).encode())
+        h.update(b"\0")
     return h.hexdigest()[:16]
+
+
+def kernel_source_hash():
+    return _code_hash(("paper_1609_01479_gb300/csrc/ld_fused.cuh", "paper_1609_01479_gb300/csrc/ld_common.cuh"))
 
 
 def fp64_source_hash():
-    h = hashlib.sha256()
-    for rel in ("paper_1609_01479_gb300/csrc/ld_generic.cuh", "paper_1609_01479_gb300/csrc/ld_common.cuh",
-                "paper_1609_01479_gb300/csrc/ld_prec_f64.cu"):
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+    return _code_hash(("paper_1609_01479_gb300/csrc/ld_generic.cuh", "paper_1609_01479_gb300/csrc/ld_common.cuh",
+                       "paper_1609_01479_gb300/csrc/ld_prec_f64.cu"))
 
 
 def recorded_fp64_ops():
