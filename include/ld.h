@@ -104,6 +104,28 @@ enum { LD_FORCE_POTENTIAL = 0, LD_FORCE_STRESS = 1 };
  *   no adjoint. Fixed at ld_create. */
 enum { LD_COLLISION_BGK = 0, LD_COLLISION_TRT = 1 };
 
+/* Rounding of the 16-bit storage forms (LD_FP16DEV, LD_BF16DEV) when a step
+ * stores its collided values; ld_init and ld_set_distributions always round
+ * to nearest. The paper fixes no storage precision; these are two readings.
+ * LD_ROUND_NEAREST: round to nearest even (default).
+ * LD_ROUND_STOCHASTIC: stochastic rounding (Connolly, Higham & Mary 2021,
+ *   "mode 1"). The deviation h (FP32) is rounded toward zero to lo; hi is the
+ *   next 16-bit value away from zero; the stored value is hi when
+ *   k * (|hi| - |lo|) < 65536 * (|h| - |lo|), else lo, for a 16-bit random
+ *   integer k: P(hi) = (|h| - |lo|)/(|hi| - |lo|) (to 2^-16), so the stored
+ *   value is h in expectation. Exact values and the largest finite
+ *   magnitude are kept. k comes from SplitMix64 (Steele, Lea & Flood 2014:
+ *   state increment gamma = 0x9E3779B97F4A7C15 and its 64-bit output mix),
+ *   counter based: for step t (steps taken since ld_init), array a (0 = f,
+ *   1 = g), direction i and site s (x + nx*(y + ny*z), N sites), the word is
+ *   the SplitMix64 output of state seed + (c + 1)*gamma (mod 2^64) with
+ *   c = ((2t + a)*5 + i/4)*N + s, and k is its bits 16*(i%4) .. 16*(i%4)+15
+ *   (the value collided at site s in direction i). Fixed seed: bitwise
+ *   reproducible runs. 16-bit forms only; not with LD_KERNEL_FUSED_TMA,
+ *   ld_step_between or the adjoint (LD_EINVAL), whose recomputation would
+ *   need the step counter of the saved state. Fixed at ld_create. */
+enum { LD_ROUND_NEAREST = 0, LD_ROUND_STOCHASTIC = 1 };
+
 enum {
     LD_OK = 0,
     LD_EINVAL = -1,     /* bad argument: dims < 4, null/host pointer, tau <= 1/2, small workspace */
@@ -122,6 +144,8 @@ typedef struct {
     int force;                 /* LD_FORCE_POTENTIAL / LD_FORCE_STRESS */
     int collision;             /* LD_COLLISION_BGK / LD_COLLISION_TRT */
     double magic;              /* TRT: (tau_f - 1/2)(tau- - 1/2) > 0 (3/16 is usual) */
+    int rounding;              /* LD_ROUND_NEAREST / LD_ROUND_STOCHASTIC */
+    unsigned long long seed;   /* stochastic rounding: seed of the random stream */
 } ld_params;
 
 typedef struct ld_ctx ld_ctx;
@@ -143,19 +167,22 @@ int ld_destroy(ld_ctx* ctx);
 /* Change the stream later calls are ordered on. */
 int ld_set_stream(ld_ctx* ctx, void* cuda_stream);
 
-/* Replace A, B, kappa, Gamma, tau_f, tau_g, the stencil and magic (precision,
- * kernel, rho0, force and collision must stay as created: LD_EINVAL
- * otherwise). Takes effect at the next launch. */
+/* Replace A, B, kappa, Gamma, tau_f, tau_g, the stencil, magic and the seed
+ * of stochastic rounding (precision, kernel, rho0, force, collision and
+ * rounding must stay as created: LD_EINVAL otherwise). Takes effect at the
+ * next launch. */
 int ld_set_params(ld_ctx* ctx, const ld_params* p);
 
 /* Initial state (equilibrium, no force): f = feq(rho, u), g = geq(phi, u, mu(phi))
  * with mu from the selected stencil's Laplacian of phi. phi: device double[N];
  * rho: device double[N] or NULL (rho0 everywhere); u: device double[3][N] or
- * NULL (at rest). Also fixes the deviation reference of LD_FP16DEV/LD_BF16DEV. */
+ * NULL (at rest). Also fixes the deviation reference of LD_FP16DEV/LD_BF16DEV
+ * and sets the step counter t of stochastic rounding to 0. */
 int ld_init(ld_ctx* ctx, const double* phi, const double* rho, const double* u);
 
 /* Advance nsteps >= 0 full timesteps (moments, phi stencil and mu, force,
- * collisions of f and g, propagation). Asynchronous. */
+ * collisions of f and g, propagation). Each step adds 1 to the step counter
+ * of stochastic rounding. Asynchronous. */
 int ld_step(ld_ctx* ctx, int nsteps);
 
 /* Macroscopic fields of the current (pre-collision) state. Each output may be
@@ -197,7 +224,8 @@ int ld_load_state(ld_ctx* ctx, const void* dev_buf);
  * ld_state_bytes() bytes, distinct, 16-byte aligned: the step kernels move
  * rows of the state with bulk copies), without touching the context's own
  * state: used to recompute a checkpointed segment into a tape of states.
- * LD_EINVAL for host, equal or misaligned buffers.
+ * LD_EINVAL for host, equal or misaligned buffers, and with
+ * LD_ROUND_STOCHASTIC.
  * fields_out (device, ld_fields_bytes(), or NULL) receives the phi and mu
  * fields of the source state ([phi npad][mu npad] in the arithmetic type),
  * which ld_adjoint_step can then reuse instead of recomputing them. */
@@ -212,7 +240,8 @@ int ld_step_between(ld_ctx* ctx, const void* src_state, void* dst_state, void* f
  *   of both collisions and of u = (j+F/2)/rho and F = -phi grad(mu), whose
  *   non-local parts are the transposed gradient and the (symmetric)
  *   Laplacian of the selected stencil; gbar_i = (1 - 1/tau_g) gbar*_i + phibar.
- * Defined for LD_FORCE_POTENTIAL with LD_COLLISION_BGK only.
+ * Defined for LD_FORCE_POTENTIAL with LD_COLLISION_BGK and LD_ROUND_NEAREST
+ * only.
  * The adjoint state is held in the arithmetic type (FP64 for LD_FP64,
  * FP32 otherwise); parameter sums are FP64 in a fixed order. */
 

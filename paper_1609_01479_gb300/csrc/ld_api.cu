@@ -95,6 +95,13 @@ bool params_ok(const ld_params* p, const char** why) {
         if (p->kernel == LD_KERNEL_FUSED || p->kernel == LD_KERNEL_FUSED_TMA)
             return *why = "the TRT collision runs on the generic kernel only", false;
     }
+    if (p->rounding != LD_ROUND_NEAREST && p->rounding != LD_ROUND_STOCHASTIC) return *why = "unknown rounding", false;
+    if (p->rounding == LD_ROUND_STOCHASTIC) {
+        if (p->precision != LD_FP16DEV && p->precision != LD_BF16DEV)
+            return *why = "stochastic rounding applies to the 16-bit storage forms only", false;
+        if (p->kernel == LD_KERNEL_FUSED_TMA)
+            return *why = "the TMA-staged kernel rounds to nearest only", false;
+    }
     return true;
 }
 
@@ -184,6 +191,7 @@ int ld_create(int nx, int ny, int nz, const ld_params* p, void* dev_workspace, s
     c->dist[0] = c->ws + L.dist;
     c->dist[1] = c->ws + L.dist + dist_one;
     c->cur = 0;
+    c->sr_step = 0;
     c->phi = c->ws + L.phi;
     c->mu = c->ws + L.mu;
     c->stress = p->force == LD_FORCE_STRESS ? c->ws + L.stress : nullptr;
@@ -230,8 +238,9 @@ int ld_set_params(ld_ctx* c, const ld_params* p) {
     if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
     if (!params_ok(p, &why)) return fail(c, LD_EINVAL, "%s", why);
     if (p->precision != c->prm.precision || p->kernel != c->prm.kernel || p->rho0 != c->prm.rho0 ||
-        p->force != c->prm.force || p->collision != c->prm.collision)
-        return fail(c, LD_EINVAL, "precision, kernel, rho0, the force form and the collision are fixed at ld_create");
+        p->force != c->prm.force || p->collision != c->prm.collision || p->rounding != c->prm.rounding)
+        return fail(c, LD_EINVAL,
+                    "precision, kernel, rho0, the force form, the collision and the rounding are fixed at ld_create");
     c->prm = *p;
     return LD_OK;
 }
@@ -241,6 +250,7 @@ int ld_init(ld_ctx* c, const double* phi, const double* rho, const double* u) {
     if (!is_device_ptr(phi)) return fail(c, LD_EINVAL, "phi must be a device pointer");
     if (!opt_device(rho) || !opt_device(u)) return fail(c, LD_EINVAL, "rho and u must be device pointers or NULL");
     c->cur = 0;
+    c->sr_step = 0;
     cudaError_t e = ld::launch_init(c, phi, rho, u);
     if (e != cudaSuccess) return cuda_fail(c, e, "ld_init");
     c->initialized = true;
@@ -255,6 +265,7 @@ int ld_step(ld_ctx* c, int nsteps) {
         cudaError_t e = ld::launch_step(c, c->dist[c->cur], c->dist[1 - c->cur]);
         if (e != cudaSuccess) return cuda_fail(c, e, "ld_step");
         c->cur ^= 1;
+        ++c->sr_step;
     }
     return LD_OK;
 }
@@ -385,14 +396,18 @@ int check_adj(ld_ctx* c) {
 extern "C" {
 
 size_t ld_adjoint_workspace_bytes(const ld_ctx* c) {
-    return c && c->prm.force == LD_FORCE_POTENTIAL && c->prm.collision == LD_COLLISION_BGK ? adj_layout_of(c).total
-                                                                                            : 0;
+    return c && c->prm.force == LD_FORCE_POTENTIAL && c->prm.collision == LD_COLLISION_BGK &&
+                   c->prm.rounding == LD_ROUND_NEAREST
+               ? adj_layout_of(c).total
+               : 0;
 }
 
 int ld_adjoint_attach(ld_ctx* c, void* dev_workspace, size_t bytes) {
     if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
     if (c->prm.force != LD_FORCE_POTENTIAL || c->prm.collision != LD_COLLISION_BGK)
         return fail(c, LD_EINVAL, "the adjoint is built for the BGK collision with F = -phi grad(mu) only");
+    if (c->prm.rounding != LD_ROUND_NEAREST)
+        return fail(c, LD_EINVAL, "the adjoint's recomputation needs round-to-nearest storage");
     const AdjLayout L = adj_layout_of(c);
     if (!is_device_ptr(dev_workspace)) return fail(c, LD_EINVAL, "adjoint workspace is not a device pointer");
     if ((uintptr_t)dev_workspace % kAlign) return fail(c, LD_EINVAL, "adjoint workspace must be 256-byte aligned");
@@ -418,6 +433,8 @@ size_t ld_fields_bytes(const ld_ctx* c) { return c ? align_up(2 * (size_t)c->geo
 int ld_step_between(ld_ctx* c, const void* src_state, void* dst_state, void* fields_out) {
     int rc = check_ready(c);
     if (rc) return rc;
+    if (c->prm.rounding != LD_ROUND_NEAREST)
+        return fail(c, LD_EINVAL, "ld_step_between has no step counter for stochastic rounding");
     if (!is_device_ptr(src_state) || !is_device_ptr(dst_state) || src_state == dst_state)
         return fail(c, LD_EINVAL, "src and dst must be distinct device state buffers");
     if ((uintptr_t)src_state % 16 || (uintptr_t)dst_state % 16)

@@ -65,6 +65,7 @@ template <> struct Prec<LD_FP16DEV> {
     static constexpr bool kDev = true;
     __device__ static float decode(store_t v, float ref) { return ref + __half2float(v); }
     __device__ static store_t encode(float x, float ref) { return __float2half_rn(x - ref); }
+    __device__ static store_t encode_sr(float x, float ref, unsigned k);
     __device__ static double decode_d(store_t v, float ref) { return (double)ref + (double)__half2float(v); }
     __device__ static store_t encode_d(double x, float ref) { return __double2half(x - (double)ref); }
 };
@@ -74,9 +75,69 @@ template <> struct Prec<LD_BF16DEV> {
     static constexpr bool kDev = true;
     __device__ static float decode(store_t v, float ref) { return ref + __bfloat162float(v); }
     __device__ static store_t encode(float x, float ref) { return __float2bfloat16_rn(x - ref); }
+    __device__ static store_t encode_sr(float x, float ref, unsigned k);
     __device__ static double decode_d(store_t v, float ref) { return (double)ref + (double)__bfloat162float(v); }
     __device__ static store_t encode_d(double x, float ref) { return __double2bfloat16(x - (double)ref); }
 };
+
+// Stochastic rounding of the FP32 deviation h to a 16-bit format with the
+// 16-bit random integer k (Connolly, Higham & Mary 2021, mode 1): lo = h
+// rounded toward zero, hi = the next value away from zero, and hi is taken
+// when k (|hi| - |lo|) < 65536 (|h| - |lo|). Both sides of the comparison are
+// exact in FP32 (|hi| - |lo| is a power of two, |h| - |lo| is exact by
+// Sterbenz's lemma or because lo = 0), so the decision is a function of h and
+// k alone. Exact values, NaN and the largest finite magnitude are kept.
+__device__ __forceinline__ bool sr_up(float h, float lo, float hi, unsigned k) {
+    const float gap = __fsub_rn(fabsf(hi), fabsf(lo));
+    const float d = __fsub_rn(fabsf(h), fabsf(lo));
+    return __fmul_rn((float)k, gap) < __fmul_rn(d, 65536.0f);
+}
+__device__ __forceinline__ __half Prec<LD_FP16DEV>::encode_sr(float x, float ref, unsigned k) {
+    const float h = x - ref;
+    const __half lo = __float2half_rz(h);
+    const float lof = __half2float(lo);
+    const unsigned short b = __half_as_ushort(lo);
+    if (lof == h || (b & 0x7fffu) == 0x7bffu) return lo;
+    const __half hi = __ushort_as_half((unsigned short)(b + 1));
+    return sr_up(h, lof, __half2float(hi), k) ? hi : lo;
+}
+__device__ __forceinline__ __nv_bfloat16 Prec<LD_BF16DEV>::encode_sr(float x, float ref, unsigned k) {
+    const float h = x - ref;
+    const __nv_bfloat16 lo = __float2bfloat16_rz(h);
+    const float lof = __bfloat162float(lo);
+    const unsigned short b = __bfloat16_as_ushort(lo);
+    if (lof == h || (b & 0x7fffu) == 0x7f7fu) return lo;
+    const __nv_bfloat16 hi = __ushort_as_bfloat16((unsigned short)(b + 1));
+    return sr_up(h, lof, __bfloat162float(hi), k) ? hi : lo;
+}
+
+// Random words of stochastic rounding: SplitMix64 (Steele, Lea & Flood 2014)
+// used as a counter-based generator. The word of counter c is the output
+// mix of the state seed + (c + 1) gamma; c = ((2t + a) 5 + q) N + s for step
+// t, array a (0 f, 1 g), quarter q = i / 4 of the directions and site s.
+constexpr unsigned long long kSrGamma = 0x9E3779B97F4A7C15ull;
+__device__ __forceinline__ unsigned long long sr_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+// The step's stream: state of (a, q, s) = base + s gamma + (5a + q) stride,
+// with base = seed + gamma + 10 t N gamma and stride = N gamma (mod 2^64).
+struct SrStream {
+    unsigned long long base, stride;
+};
+inline SrStream sr_stream(unsigned long long seed, unsigned long long t, long long n) {
+    const unsigned long long ng = (unsigned long long)n * kSrGamma;
+    return SrStream{seed + kSrGamma + 10ull * t * ng, ng};
+}
+// 16-bit random integer of direction i of array a at a site whose stream
+// state is st = base + s gamma; w caches the word of the current quarter
+// (the loops over i are unrolled, so i % 4 == 0 refreshes it).
+__device__ __forceinline__ unsigned sr_key(const SrStream& r, unsigned long long st, int a, int i,
+                                           unsigned long long& w) {
+    if ((i & 3) == 0) w = sr_mix(st + (unsigned long long)(5 * a + (i >> 2)) * r.stride);
+    return (unsigned)(w >> (16 * (i & 3))) & 0xffffu;
+}
 
 // Lattice geometry. npad: component stride of every SoA array (>= n, a
 // multiple of 64 so each component starts 256-byte aligned for 32-bit data).

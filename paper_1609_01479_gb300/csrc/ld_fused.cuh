@@ -48,13 +48,14 @@ __device__ __forceinline__ int wrap_once(int a, int n) { return a < 0 ? a + n : 
 // in one register each; 64-bit only where 19 npad does not fit in it.
 // ISO: the 19-point isotropic stencils (mu's Laplacian over the phi ring,
 // grad mu over the mu ring, corners included) instead of the 7-point ones.
-template <int P, int TY, class I, bool ISO>
+// SR: stochastic rounding of the 16-bit stores, from the stream `sr`.
+template <int P, int TY, class I, bool ISO, bool SR>
 __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     k_step_fused(Geom g, Model<typename Prec<P>::real_t> m, int zc,
                  const typename Prec<P>::store_t* __restrict__ fs, const typename Prec<P>::store_t* __restrict__ gs,
                  typename Prec<P>::store_t* __restrict__ fd, typename Prec<P>::store_t* __restrict__ gd,
                  const float* __restrict__ ref_g, typename Prec<P>::real_t* __restrict__ phi_out,
-                 typename Prec<P>::real_t* __restrict__ mu_out) {
+                 typename Prec<P>::real_t* __restrict__ mu_out, SrStream sr) {
     using R = typename Prec<P>::real_t;
     using S = typename Prec<P>::store_t;
     constexpr int PW = kTX + 4, PH = TY + 4;  // phi ring plane
@@ -186,11 +187,16 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
         R ux, uy, uz;
         guo_velocity(rho, jx, jy, jz, Fx, Fy, Fz, ux, uy, uz);
         collide_f(f, rho, ux, uy, uz, Fx, Fy, Fz, m);
+        const unsigned long long sr_st = SR ? sr.base + (unsigned long long)s * kSrGamma : 0ull;
+        unsigned long long sr_w = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int d = s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
                           (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
-            __stcs(fd + i * npad + d, Prec<P>::encode(f[i], refs[i]));
+            if constexpr (SR)
+                __stcs(fd + i * npad + d, Prec<P>::encode_sr(f[i], refs[i], sr_key(sr, sr_st, 0, i, sr_w)));
+            else
+                __stcs(fd + i * npad + d, Prec<P>::encode(f[i], refs[i]));
         }
 
         R gg[Q];
@@ -206,7 +212,10 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
         for (int i = 0; i < Q; ++i) {
             const int d = s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
                           (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
-            __stcs(gd + i * npad + d, Prec<P>::encode(gg[i], refs[Q + i]));
+            if constexpr (SR)
+                __stcs(gd + i * npad + d, Prec<P>::encode_sr(gg[i], refs[Q + i], sr_key(sr, sr_st, 1, i, sr_w)));
+            else
+                __stcs(gd + i * npad + d, Prec<P>::encode(gg[i], refs[Q + i]));
         }
     }
 }
@@ -234,14 +243,14 @@ int choose_zc(int nx, int ny, int nz, int num_sms = 152, int per_sm = 2) {
     return best;
 }
 
-template <int P, class I, bool ISO>
+template <int P, class I, bool ISO, bool SR>
 cudaError_t launch_fused(ld_ctx* c, const void* src, void* dst, void* fields) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     constexpr size_t kRingBytes = sizeof(S) == 2 ? 3 * (size_t)Q * kTY * kTX * sizeof(S) : 0;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_fused<P, kTY, I, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_step_fused<P, kTY, I, ISO, SR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kRingBytes);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -249,18 +258,31 @@ cudaError_t launch_fused(ld_ctx* c, const void* src, void* dst, void* fields) {
     const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
     const int zc = choose_zc(g.nx, g.ny, g.nz, c->num_sms, fused_ctas_per_sm<P>());
     const dim3 grid(g.nx / kTX, g.ny / kTY, g.nz / zc);
-    k_step_fused<P, kTY, I, ISO><<<grid, kTX * kTY, kRingBytes, c->stream>>>(
+    k_step_fused<P, kTY, I, ISO, SR><<<grid, kTX * kTY, kRingBytes, c->stream>>>(
         g, model_of<R>(c->prm), zc, (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
-        (S*)g_part(c, dst), c->ref, fields ? (R*)fields : nullptr, fields ? (R*)fields + c->geom.npad : nullptr);
+        (S*)g_part(c, dst), c->ref, fields ? (R*)fields : nullptr, fields ? (R*)fields + c->geom.npad : nullptr,
+        sr_stream(c->prm.seed, c->sr_step, c->geom.n));
     return cudaGetLastError();
 }
 
-template <int P>
-cudaError_t step_fused_p(ld_ctx* c, const void* src, void* dst, void* fields) {
+template <int P, bool SR>
+cudaError_t step_fused_r(ld_ctx* c, const void* src, void* dst, void* fields) {
     const bool small = (long long)Q * c->geom.npad <= 0x7fffffffLL;
     if (c->prm.stencil == LD_STENCIL_19)
-        return small ? launch_fused<P, int, true>(c, src, dst, fields) : launch_fused<P, long long, true>(c, src, dst, fields);
-    return small ? launch_fused<P, int, false>(c, src, dst, fields) : launch_fused<P, long long, false>(c, src, dst, fields);
+        return small ? launch_fused<P, int, true, SR>(c, src, dst, fields)
+                     : launch_fused<P, long long, true, SR>(c, src, dst, fields);
+    return small ? launch_fused<P, int, false, SR>(c, src, dst, fields)
+                 : launch_fused<P, long long, false, SR>(c, src, dst, fields);
+}
+
+// Stochastic rounding exists for the 16-bit forms only (it is refused at
+// ld_create for the others).
+template <int P>
+cudaError_t step_fused_p(ld_ctx* c, const void* src, void* dst, void* fields) {
+    if constexpr (Prec<P>::kDev) {
+        if (c->prm.rounding == LD_ROUND_STOCHASTIC) return step_fused_r<P, true>(c, src, dst, fields);
+    }
+    return step_fused_r<P, false>(c, src, dst, fields);
 }
 
 }  // namespace

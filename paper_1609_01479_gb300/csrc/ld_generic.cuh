@@ -181,10 +181,11 @@ constexpr int rows_blocks_per_sm() {
 }
 
 // Stage 3: force, velocity, collisions of f and g, and propagation (push: the
-// post-collision value of direction i goes to x + c_i) with streaming stores.
-template <int P, class I>
+// post-collision value of direction i goes to x + c_i) with streaming stores;
+// SR: the 16-bit stores rounded stochastically from the stream `sr`.
+template <int P, class I, bool SR>
 __global__ void __launch_bounds__(kRowThreads, rows_blocks_per_sm<P>())
-    k_collide(RowGeom rg, I npad, Model<typename Prec<P>::real_t> m, const typename Prec<P>::store_t* __restrict__ fs,
+    k_collide(RowGeom rg, I npad, Model<typename Prec<P>::real_t> m, SrStream sr, const typename Prec<P>::store_t* __restrict__ fs,
               const typename Prec<P>::store_t* __restrict__ gs, typename Prec<P>::store_t* __restrict__ fd,
               typename Prec<P>::store_t* __restrict__ gd, const typename Prec<P>::real_t* __restrict__ phi,
               const typename Prec<P>::real_t* __restrict__ mu, const float* __restrict__ ref,
@@ -235,11 +236,16 @@ __global__ void __launch_bounds__(kRowThreads, rows_blocks_per_sm<P>())
         collide_f_trt(f, rho, ux, uy, uz, Fx, Fy, Fz, m);
     else
         collide_f(f, rho, ux, uy, uz, Fx, Fy, Fz, m);
+    const unsigned long long sr_st = SR ? sr.base + (unsigned long long)s * kSrGamma : 0ull;
+    unsigned long long sr_w = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int d = s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
                       (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
-        __stcs(fd + i * npad + d, Prec<P>::encode(f[i], refs[i]));
+        if constexpr (SR)
+            __stcs(fd + i * npad + d, Prec<P>::encode_sr(f[i], refs[i], sr_key(sr, sr_st, 0, i, sr_w)));
+        else
+            __stcs(fd + i * npad + d, Prec<P>::encode(f[i], refs[i]));
     }
     R gg[Q];
 #pragma unroll
@@ -249,7 +255,10 @@ __global__ void __launch_bounds__(kRowThreads, rows_blocks_per_sm<P>())
     for (int i = 0; i < Q; ++i) {
         const int d = s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
                       (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
-        __stcs(gd + i * npad + d, Prec<P>::encode(gg[i], refs[Q + i]));
+        if constexpr (SR)
+            __stcs(gd + i * npad + d, Prec<P>::encode_sr(gg[i], refs[Q + i], sr_key(sr, sr_st, 1, i, sr_w)));
+        else
+            __stcs(gd + i * npad + d, Prec<P>::encode(gg[i], refs[Q + i]));
     }
 }
 
@@ -542,7 +551,7 @@ cudaError_t phi_mu_p(ld_ctx* c, const void* state, void* fields = nullptr) {
     return offsets_fit_int(c) ? phi_mu_rows<P, int>(c, state, fields) : phi_mu_rows<P, long long>(c, state, fields);
 }
 
-template <int P, class I>
+template <int P, class I, bool SR>
 cudaError_t collide_rows(ld_ctx* c, const void* src, void* dst, void* fields) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
@@ -553,16 +562,25 @@ cudaError_t collide_rows(ld_ctx* c, const void* src, void* dst, void* fields) {
     if (c->stress)
         k_stress<R, I><<<row_blocks(c->geom), kRowThreads, 0, c->stream>>>(row_geom(c->geom), (I)c->geom.npad,
                                                                            model_of<R>(c->prm), phi, (R*)c->stress);
-    k_collide<P, I><<<row_blocks(c->geom), kRowThreads, 0, c->stream>>>(
-        row_geom(c->geom), (I)c->geom.npad, model_of<R>(c->prm), (const S*)f_part(c, src), (const S*)g_part(c, src),
+    k_collide<P, I, SR><<<row_blocks(c->geom), kRowThreads, 0, c->stream>>>(
+        row_geom(c->geom), (I)c->geom.npad, model_of<R>(c->prm), sr_stream(c->prm.seed, c->sr_step, c->geom.n),
+        (const S*)f_part(c, src), (const S*)g_part(c, src),
         (S*)f_part(c, dst), (S*)g_part(c, dst), phi, mu, c->ref, (const R*)c->stress);
     return cudaGetLastError();
 }
 
+template <int P, bool SR>
+cudaError_t collide_r(ld_ctx* c, const void* src, void* dst, void* fields) {
+    return offsets_fit_int(c) ? collide_rows<P, int, SR>(c, src, dst, fields)
+                              : collide_rows<P, long long, SR>(c, src, dst, fields);
+}
+
 template <int P>
 cudaError_t collide_p(ld_ctx* c, const void* src, void* dst, void* fields) {
-    return offsets_fit_int(c) ? collide_rows<P, int>(c, src, dst, fields)
-                              : collide_rows<P, long long>(c, src, dst, fields);
+    if constexpr (Prec<P>::kDev) {
+        if (c->prm.rounding == LD_ROUND_STOCHASTIC) return collide_r<P, true>(c, src, dst, fields);
+    }
+    return collide_r<P, false>(c, src, dst, fields);
 }
 
 template <int P>

@@ -49,6 +49,7 @@ struct ld_ctx {
     cudaStream_t stream;
     bool initialized;
     int step_kernel;  // ld::StepKernel
+    unsigned long long sr_step;  // step counter t of stochastic rounding (0 at ld_init)
     // adjoint (attached with ld_adjoint_attach): two adjoint states
     // fbar[19][npad] + gbar[19][npad] in the arithmetic type, per-site scratch,
     // per-block FP64 partials (2 per block)

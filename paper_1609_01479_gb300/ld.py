@@ -33,6 +33,8 @@ LD_FORCE_POTENTIAL, LD_FORCE_STRESS = 0, 1
 FORCES = {"potential": LD_FORCE_POTENTIAL, "stress": LD_FORCE_STRESS}
 LD_COLLISION_BGK, LD_COLLISION_TRT = 0, 1
 COLLISIONS = {"bgk": LD_COLLISION_BGK, "trt": LD_COLLISION_TRT}
+LD_ROUND_NEAREST, LD_ROUND_STOCHASTIC = 0, 1
+ROUNDINGS = {"nearest": LD_ROUND_NEAREST, "stochastic": LD_ROUND_STOCHASTIC}
 Q = 19
 
 
@@ -41,7 +43,7 @@ class LdParams(ctypes.Structure):
                 ("Gamma", ctypes.c_double), ("tau_f", ctypes.c_double), ("tau_g", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("stencil", ctypes.c_int), ("force", ctypes.c_int), ("collision", ctypes.c_int),
-                ("magic", ctypes.c_double)]
+                ("magic", ctypes.c_double), ("rounding", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
 class LdError(RuntimeError):
@@ -125,16 +127,19 @@ def _call(name, ctx, *args):
 
 def make_params(A=-0.0625, B=0.0625, kappa=0.04, Gamma=0.5, tau_f=1.0, tau_g=1.0, rho0=1.0,
                 precision="fp32", kernel="auto", stencil=7, force="potential", collision="bgk",
-                magic=0.1875) -> LdParams:
+                magic=0.1875, rounding="nearest", seed=0) -> LdParams:
     """ld_params; stencil is 7 (7-point Laplacian, central difference) or 19
     (the 19-point isotropic forms); force is "potential" (-phi grad mu) or
     "stress" (-div P); collision is "bgk" or "trt" (with the magic parameter
-    (tau_f - 1/2)(tau- - 1/2))."""
+    (tau_f - 1/2)(tau- - 1/2)); rounding of the 16-bit storage forms is
+    "nearest" or "stochastic" (with a 64-bit seed)."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     kern = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
     frc = FORCES[force] if isinstance(force, str) else int(force)
     col = COLLISIONS[collision] if isinstance(collision, str) else int(collision)
-    return LdParams(A, B, kappa, Gamma, tau_f, tau_g, rho0, prec, kern, STENCILS[int(stencil)], frc, col, magic)
+    rnd = ROUNDINGS[rounding] if isinstance(rounding, str) else int(rounding)
+    return LdParams(A, B, kappa, Gamma, tau_f, tau_g, rho0, prec, kern, STENCILS[int(stencil)], frc, col, magic,
+                    rnd, int(seed) & 0xFFFFFFFFFFFFFFFF)
 
 
 # ---------------------------------------------------------------------------
@@ -303,9 +308,12 @@ class LdSim:
             model = dict(model, force=FORCES[model["force"]])
         if isinstance(model.get("collision"), str):
             model = dict(model, collision=COLLISIONS[model["collision"]])
+        if isinstance(model.get("rounding"), str):
+            model = dict(model, rounding=ROUNDINGS[model["rounding"]])
         kw.update(model)
-        self.params = LdParams(*[kw[f[0]] for f in LdParams._fields_])
-        ld_set_params(self.ctx, self.params)
+        params = LdParams(*[kw[f[0]] for f in LdParams._fields_])
+        ld_set_params(self.ctx, params)  # raises, keeping the old parameters, if refused
+        self.params = params
 
     def init(self, phi, rho=None, u=None):
         phi = torch.as_tensor(phi, dtype=torch.float64, device=self.device).contiguous()

@@ -5,9 +5,11 @@ also relative to rho - 1, which is what the dynamics moves).
   1. 16^3 spinodal, 10 and 100 steps: every precision against the oracle.
   2. 128^3 spinodal, 1000 steps: FP64 and FP32 GPU against the oracle at
      steps 100 and 1000.
-  3. 256^3 droplet (R = 32), 2000 steps: FP32, FP16-dev and BF16-dev against
-     the FP64 GPU path (which matches the oracle to 1e-12 at the sizes the
-     oracle can run; 256^3 x 2000 steps would take it about half an hour).
+  3. 256^3 droplet (R = 32), 2000 steps: FP32, FP16-dev and BF16-dev (with
+     round-to-nearest and with stochastic rounding) against the FP64 GPU
+     path (which matches the oracle to 1e-12 at the sizes the oracle can
+     run; 256^3 x 2000 steps would take it about half an hour), with the
+     drift of total mass and total phi.
 
 Bounds: FP64 1e-12; FP32 phi 1e-5 (the headline bound at 256^3); the 16-bit
 forms 2^-p sqrt(steps) (p = 11 FP16, 8 BF16), the rounding of a stored
@@ -52,16 +54,18 @@ def errors(m, ref):
             "phi_maxabs": float(np.abs(m["phi"] - ref["phi"]).max())}
 
 
-def gpu_moments(ld, phi0, precision, checkpoints):
+def gpu_moments(ld, phi0, precision, checkpoints, **model):
     nz, ny, nx = phi0.shape
-    sim = ld.LdSim(nx, ny, nz, precision=precision)
+    sim = ld.LdSim(nx, ny, nz, precision=precision, **model)
     sim.init(torch.from_numpy(phi0).cuda())
     out, t = {}, 0
+    out["totals0"] = sim.totals().cpu().numpy()
     for c in checkpoints:
         sim.step(c - t)
         t = c
         m = sim.moments()
         out[c] = {k: m[k].cpu().numpy() for k in ("phi", "rho", "u")}
+        out[c]["totals"] = sim.totals().cpu().numpy()
     sim.close()
     return out
 
@@ -122,9 +126,16 @@ def test_config3_droplet_256cube_2000_steps(ld):
     phi0 = inputs.droplet_phi(n, n, n, R, 1.0, xi)
     ref = gpu_moments(ld, phi0, "fp64", (steps,))[steps]
     table = {}
-    for prec in ("fp32", "fp16dev", "bf16dev"):
-        got = gpu_moments(ld, phi0, prec, (steps,))[steps]
+    runs = [("fp32", {}), ("fp16dev", {}), ("bf16dev", {}),
+            ("fp16dev", {"rounding": "stochastic", "seed": 3}), ("bf16dev", {"rounding": "stochastic", "seed": 3})]
+    for prec, model in runs:
+        out = gpu_moments(ld, phi0, prec, (steps,), **model)
+        got = out[steps]
         e = errors(got, ref)
-        table[prec] = e
-        assert e["phi"] <= BOUND[prec](steps), (prec, e)
+        t0, t1 = out["totals0"], got["totals"]
+        e["mass_drift"] = float(abs(t1[0] - t0[0]) / abs(t0[0]))
+        e["phi_drift"] = float(abs(t1[1] - t0[1]) / np.abs(phi0).sum())
+        name = prec + ("-sr" if model else "")
+        table[name] = e
+        assert e["phi"] <= BOUND[prec](steps), (name, e)
     report("256^3 droplet R=32, 2000 steps, vs FP64 GPU", table)
