@@ -43,6 +43,15 @@ constexpr int fused_ctas_per_sm() {
 // Periodic image of a coordinate at most one period outside [0, n).
 __device__ __forceinline__ int wrap_once(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+// A 16-bit storage word from its bit pattern.
+template <class T>
+__device__ __forceinline__ T bits16(unsigned b) {
+    const unsigned short u = (unsigned short)b;
+    T v;
+    memcpy(&v, &u, 2);
+    return v;
+}
+
 // I: type of the element offsets i * npad + s. A 32-bit offset keeps the
 // 19 per-direction offsets, which the compiler holds for the whole kernel,
 // in one register each; 64-bit only where 19 npad does not fit in it.
@@ -81,23 +90,55 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     const uint64_t keep_l2 = make_l2_evict_last_policy(), drop_l2 = make_l2_evict_first_policy();
     __syncthreads();
 
-    // phi of plane zp over the tile + 2-halo, into ring slot `slot`.
+    // phi of plane zp over the tile + 2-halo, into ring slot `slot`. With
+    // 32- and 16-bit storage each thread sums two x-adjacent sites from
+    // paired loads: 216 pairs, one round for 256 threads, half the load and
+    // address instructions. The halo's x range starts at an even x and nx is
+    // even, so a pair never straddles the periodic wrap; each site's sum over
+    // i keeps its order, so phi is the same as from single loads.
     auto phi_plane = [&](int zp, int slot) {
         const int zoff = wrap_once(zp, nz) * plane;
-        for (int idx = tid; idx < PW * PH; idx += NT) {
-            const int hx = idx % PW, hy = idx / PW;
-            const int gx = wrap_once(x0 + hx - 2, nx), gy = wrap_once(y0 + hy - 2, ny);
-            const int s = zoff + gy * nx + gx;
-            const bool interior = kKeepG && hx >= 2 && hx < kTX + 2 && hy >= 2 && hy < TY + 2;
-            S* keep = gring + ((size_t)slot * Q * TY + (hy - 2)) * kTX + (hx - 2);
-            R acc = R(0);
+        if constexpr (sizeof(S) <= 4) {
+            constexpr int PW2 = PW / 2;
+            for (int idx = tid; idx < PW2 * PH; idx += NT) {
+                const int hx = 2 * (idx % PW2), hy = idx / PW2;
+                const int gx = wrap_once(x0 + hx - 2, nx), gy = wrap_once(y0 + hy - 2, ny);
+                const int s = zoff + gy * nx + gx;  // even
+                const bool interior = kKeepG && hx >= 2 && hx < kTX + 2 && hy >= 2 && hy < TY + 2;
+                S* keep = gring + ((size_t)slot * Q * TY + (hy - 2)) * kTX + (hx - 2);
+                R a0 = R(0), a1 = R(0);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const S v = ld_l2_hint(gs + i * npad + s, keep_l2);
-                acc += Prec<P>::decode(v, refs[Q + i]);
-                if (interior) keep[i * (TY * kTX)] = v;
+                for (int i = 0; i < Q; ++i) {
+                    if constexpr (sizeof(S) == 4) {
+                        const float2 v = ld_l2_hint_pair(gs + i * npad + s, keep_l2);
+                        a0 += v.x;
+                        a1 += v.y;
+                    } else {
+                        const unsigned v = ld_l2_hint_pair(gs + i * npad + s, keep_l2);
+                        a0 += Prec<P>::decode(bits16<S>(v & 0xffffu), refs[Q + i]);
+                        a1 += Prec<P>::decode(bits16<S>(v >> 16), refs[Q + i]);
+                        if (interior) *reinterpret_cast<unsigned*>(keep + i * (TY * kTX)) = v;
+                    }
+                }
+                phis[slot][hy][hx] = a0;
+                phis[slot][hy][hx + 1] = a1;
             }
-            phis[slot][hy][hx] = acc;
+        } else {
+            for (int idx = tid; idx < PW * PH; idx += NT) {
+                const int hx = idx % PW, hy = idx / PW;
+                const int gx = wrap_once(x0 + hx - 2, nx), gy = wrap_once(y0 + hy - 2, ny);
+                const int s = zoff + gy * nx + gx;
+                const bool interior = kKeepG && hx >= 2 && hx < kTX + 2 && hy >= 2 && hy < TY + 2;
+                S* keep = gring + ((size_t)slot * Q * TY + (hy - 2)) * kTX + (hx - 2);
+                R acc = R(0);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const S v = ld_l2_hint(gs + i * npad + s, keep_l2);
+                    acc += Prec<P>::decode(v, refs[Q + i]);
+                    if (interior) keep[i * (TY * kTX)] = v;
+                }
+                phis[slot][hy][hx] = acc;
+            }
         }
     };
     // mu over the tile + 1-halo from three phi slots (below, middle, above).

@@ -104,6 +104,20 @@ LD_DEFINE_L2_HINT_LOADS(ld_l2_hint, )
 LD_DEFINE_L2_HINT_LOADS(ld_l2_hint_now, volatile)
 #undef LD_DEFINE_L2_HINT_LOADS
 
+// Two consecutive storage words (8- or 4-byte aligned) with an L2 policy:
+// FP32 as a pair of floats, the 16-bit forms as their raw 32-bit pattern
+// (low half = the lower address).
+__device__ __forceinline__ float2 ld_l2_hint_pair(const float* p, uint64_t pol) {
+    float2 v;
+    asm("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ unsigned ld_l2_hint_pair(const void* p, uint64_t pol) {
+    unsigned v;
+    asm("ld.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
