@@ -704,3 +704,66 @@ def test_tangent_linear_with_trt(orc):
     fd = (orc.loss(phi0 + h * dphi, target, prm + h * dprm, steps) -
           orc.loss(phi0 - h * dphi, target, prm - h * dprm, steps)) / (2 * h)
     assert dL == pytest.approx(fd, rel=1e-7)
+
+
+# --------------------------------------------------------------------------
+# The discrete flat interface: the 1-D solution of the discrete equilibrium
+# condition is an exact fixed point of the whole step.
+
+
+def _discrete_interface(n, A, B, kappa, guess):
+    """Newton solve of A phi + B phi^3 - kappa (phi(x+1) + phi(x-1) - 2 phi)
+    = mu_c on a periodic 1-D lattice of n sites, with mu_c unknown and the
+    total of phi fixed to that of the guess. Returns (phi, mu_c)."""
+    phi = guess.astype(np.float64).copy()
+    total = phi.sum()
+    mu = 0.0
+    eye = np.eye(n)
+    shift = np.roll(eye, 1, axis=1) + np.roll(eye, -1, axis=1)
+    for _ in range(60):
+        lap = np.roll(phi, 1) + np.roll(phi, -1) - 2 * phi
+        r = np.concatenate([A * phi + B * phi ** 3 - kappa * lap - mu, [phi.sum() - total]])
+        if np.abs(r).max() < 1e-15:
+            break
+        J = np.zeros((n + 1, n + 1))
+        J[:n, :n] = np.diag(A + 3 * B * phi ** 2 + 2 * kappa) - kappa * shift
+        J[:n, n] = -1.0
+        J[n, :n] = 1.0
+        d = np.linalg.solve(J, -r)
+        phi += d[:n]
+        mu += d[n]
+    return phi, mu
+
+
+@pytest.mark.parametrize("kappa", [0.04, 0.08])
+@pytest.mark.parametrize("taus", [(1.0, 1.0), (0.8, 1.3)])
+def test_discrete_flat_interface_is_a_fixed_point(orc, kappa, taus):
+    """The discrete 1-D equilibrium (uniform mu with the 7-point Laplacian,
+    two interfaces normal to x, solved by Newton here) is left unchanged by
+    every step to 1e-12, with u = 0: mu uniform makes F = 0, and for a
+    profile along x the propagated parts of g^eq from the axis and the
+    diagonal directions cancel in phi for any shift (the rest, axis and
+    diagonal weights of g^eq at u = 0 are 5/6, 1/18, -1/72 per unit phi), so
+    phi never moves whatever the relaxation times. Catches a wrong
+    coefficient in mu or g^eq, a wrong Laplacian or propagation; a profile
+    solved with kappa off by 1 % moves by more than 1e-4."""
+    A, B = -0.0625, 0.0625
+    n = 64
+    x = np.arange(n)
+    xi = math.sqrt(-2 * kappa / A)
+    guess = np.tanh((x - 15.5) / xi) * np.tanh((47.5 - x) / xi)
+    phi1, mu_c = _discrete_interface(n, A, B, kappa, guess)
+    assert abs(phi1.max() - 1.0) < 1e-3 and abs(phi1.min() + 1.0) < 1e-3  # the two bulk phases
+    prm = orc.param_vector(kappa=kappa, tau_f=taus[0], tau_g=taus[1])
+    phi3 = np.broadcast_to(phi1, (4, 4, n)).copy()
+    f, g = orc.init(phi3, prm)
+    f, g = orc.step(f, g, prm, 20)
+    m = orc.macros(f, g, prm)
+    assert np.abs(m["phi"] - phi3).max() < 1e-12
+    assert np.abs(m["u"]).max() < 1e-13
+    assert np.abs(m["mu"] - mu_c).max() < 1e-12
+    # teeth: the solution for a kappa 1 % off is not a fixed point
+    phi_off, _ = _discrete_interface(n, A, B, 1.01 * kappa, guess)
+    f, g = orc.init(np.broadcast_to(phi_off, (4, 4, n)).copy(), prm)
+    f, g = orc.step(f, g, prm, 20)
+    assert np.abs(orc.macros(f, g, prm)["phi"] - phi_off).max() > 1e-4
