@@ -737,7 +737,8 @@ def _discrete_interface(n, A, B, kappa, guess):
 
 @pytest.mark.parametrize("kappa", [0.04, 0.08])
 @pytest.mark.parametrize("taus", [(1.0, 1.0), (0.8, 1.3)])
-def test_discrete_flat_interface_is_a_fixed_point(orc, kappa, taus):
+@pytest.mark.parametrize("stencil", [7, 19])
+def test_discrete_flat_interface_is_a_fixed_point(orc, kappa, taus, stencil):
     """The discrete 1-D equilibrium (uniform mu with the 7-point Laplacian,
     two interfaces normal to x, solved by Newton here) is left unchanged by
     every step to 1e-12, with u = 0: mu uniform makes F = 0, and for a
@@ -746,7 +747,9 @@ def test_discrete_flat_interface_is_a_fixed_point(orc, kappa, taus):
     diagonal weights of g^eq at u = 0 are 5/6, 1/18, -1/72 per unit phi), so
     phi never moves whatever the relaxation times. Catches a wrong
     coefficient in mu or g^eq, a wrong Laplacian or propagation; a profile
-    solved with kappa off by 1 % moves by more than 1e-4."""
+    solved with kappa off by 1 % moves by more than 1e-4. On a profile along
+    x the 19-point Laplacian equals the 7-point one (1/3 of the axis pair
+    plus 4 x 1/6 of the diagonal pairs), so the same solution serves both."""
     A, B = -0.0625, 0.0625
     n = 64
     x = np.arange(n)
@@ -754,7 +757,7 @@ def test_discrete_flat_interface_is_a_fixed_point(orc, kappa, taus):
     guess = np.tanh((x - 15.5) / xi) * np.tanh((47.5 - x) / xi)
     phi1, mu_c = _discrete_interface(n, A, B, kappa, guess)
     assert abs(phi1.max() - 1.0) < 1e-3 and abs(phi1.min() + 1.0) < 1e-3  # the two bulk phases
-    prm = orc.param_vector(kappa=kappa, tau_f=taus[0], tau_g=taus[1])
+    prm = orc.param_vector(kappa=kappa, tau_f=taus[0], tau_g=taus[1], stencil=stencil)
     phi3 = np.broadcast_to(phi1, (4, 4, n)).copy()
     f, g = orc.init(phi3, prm)
     f, g = orc.step(f, g, prm, 20)
