@@ -90,6 +90,17 @@ __global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<P>())
             gmz = R(0.5) * (mu[site_of(g, x, y, zp)] - mu[site_of(g, x, y, zm)]);
         }
         const R Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
+        // reverse propagation: the values pushed from x along c_i. They do
+        // not depend on the forward moments, so they are loaded together with
+        // the tape values and both sets of loads are in flight at once.
+        R fbs[Q], gbs[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const long long o = site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny),
+                                        step_coord(z, cz(i), g.nz));
+            fbs[i] = fb1[i * g.npad + o];
+            gbs[i] = gb1[i * g.npad + o] + pb1[o];
+        }
         R f[Q];
         R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
@@ -110,15 +121,9 @@ __global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<P>())
         R Fcx = R(0), Fcy = R(0), Fcz = R(0);  // sum of c_i x (scalar) terms of Fbar
         R F_u = R(0);                          // Fbar += F_u u
         R phib_l = R(0), mub_l = R(0);
-        R fbs[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            // reverse propagation: the value pushed from x along c_i
-            const long long o = site_of(g, step_coord(x, cx(i), g.nx), step_coord(y, cy(i), g.ny),
-                                        step_coord(z, cz(i), g.nz));
-            fbs[i] = fb1[i * g.npad + o];
-            const R gbs = gb1[i * g.npad + o] + pb1[o];
-            gb0[i * g.npad + s] = (R(1) - m.omega_g) * gbs;
+            gb0[i * g.npad + s] = (R(1) - m.omega_g) * gbs[i];
             const R w = wgt<R>(i);
             const R cu = cdot(i, ux, uy, uz);
             const R cF = cdot(i, Fx, Fy, Fz);
@@ -132,7 +137,7 @@ __global__ void __launch_bounds__(kAdjThreads, adj_ctas_per_sm<P>())
             rhob += feqb * w * base;
             const R tfe = feqb * w * rho;
             // g collision: g* = (1-w_g) g + w_g geq
-            const R tg = m.omega_g * gbs * w;
+            const R tg = m.omega_g * gbs[i] * w;
             phib_l += tg * (R(1) + R(3) * cu - R(1.5) * R(c2(i) - 1) + R(4.5) * cu * cu - R(1.5) * uu);
             mub_l += tg * R(4.5) * m.Gamma * R(c2(i) - 1);
             // d feq/du = w rho ((3 + 9cu) c - 3u); d S/du = w (9 cF c - 3F);
