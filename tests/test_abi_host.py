@@ -87,3 +87,33 @@ def test_create_rejects_null_workspace_and_bad_dims(ld):
     assert rc == ld.LD_EINVAL
     assert "tau" in ld.ld_last_error(None)
     assert lib.ld_destroy(None) == ld.LD_OK
+
+
+def test_workspace_bytes_validates_the_options(ld):
+    """The option fields of ld_params are read at their places in the
+    struct and combined as the header states: pure host logic."""
+    ws = ld.ld_workspace_bytes
+    base = ws(32, 8, 8, ld.make_params(precision="fp32"))
+    assert base > 0
+    # 19-point stencils: not on the TMA-staged kernel
+    assert ws(32, 8, 8, ld.make_params(precision="fp32", stencil=19)) == base
+    assert ws(32, 8, 8, ld.make_params(precision="fp32", stencil=19, kernel="fused_tma")) == 0
+    # the stress force: generic kernel only, six stress fields in the workspace
+    stress = ws(32, 8, 8, ld.make_params(precision="fp32", force="stress"))
+    assert stress >= base + 6 * 32 * 8 * 8 * 4
+    for kernel in ("fused", "fused_tma"):
+        assert ws(32, 8, 8, ld.make_params(precision="fp32", force="stress", kernel=kernel)) == 0
+    assert ws(32, 8, 8, ld.make_params(precision="fp32", force=7)) == 0
+    # TRT: generic kernel only, positive magic parameter
+    assert ws(32, 8, 8, ld.make_params(precision="fp32", collision="trt")) == base
+    assert ws(32, 8, 8, ld.make_params(precision="fp32", collision="trt", kernel="fused")) == 0
+    assert ws(32, 8, 8, ld.make_params(precision="fp32", collision="trt", magic=0.0)) == 0
+    assert ws(32, 8, 8, ld.make_params(precision="fp32", collision=3)) == 0
+    # stochastic rounding: the 16-bit forms only, not on the TMA-staged kernel
+    for prec in ("fp16dev", "bf16dev"):
+        nearest = ws(32, 8, 8, ld.make_params(precision=prec))
+        assert ws(32, 8, 8, ld.make_params(precision=prec, rounding="stochastic", seed=2**64 - 1)) == nearest
+        assert ws(32, 8, 8, ld.make_params(precision=prec, rounding="stochastic", kernel="fused_tma")) == 0
+    for prec in ("fp64", "fp32"):
+        assert ws(32, 8, 8, ld.make_params(precision=prec, rounding="stochastic")) == 0
+    assert ws(32, 8, 8, ld.make_params(precision="fp16dev", rounding=2)) == 0
