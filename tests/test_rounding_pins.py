@@ -124,3 +124,22 @@ def test_keys_are_uniform_and_distinct_per_stream():
     chi2 = ((hist - expected) ** 2 / expected).sum()
     assert chi2 < 400  # 255 degrees of freedom: mean 255, sd 22.6
     assert (kf == kg).mean() < 1e-3 and (kf == k1).mean() < 1e-3
+
+
+def test_bf16_round_nearest_matches_torch():
+    """bf16 round-to-nearest-even against PyTorch's own float32 -> bfloat16
+    conversion (a third implementation), on random values across the range,
+    exact ties (half a unit above a pattern, odd and even) and subnormals."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(17)
+    bits = rng.integers(0, 2**32, 200000, dtype=np.uint64).astype(np.uint32)
+    h = bits.view(np.float32)
+    h = h[np.isfinite(h)]
+    base = rng.integers(0, 2**15, 4000, dtype=np.uint32) << np.uint32(16)
+    ties = (base | np.uint32(0x8000)).view(np.float32)               # exactly half a unit
+    sub = (rng.integers(1, 2**23, 4000, dtype=np.uint32)).view(np.float32)  # float32 subnormals
+    ties = ties[np.isfinite(ties)]  # NaN patterns are not a rounding question
+    for x in (h, ties, sub, -ties, -sub):
+        ours = R.round_nearest(x, "bf16")
+        theirs = torch.from_numpy(x.copy()).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        assert np.array_equal(ours, theirs)
