@@ -41,6 +41,8 @@ VALUES_PER_SITE = 76  # 2 x 19 distributions, read + write
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "MLUPS & % of HBM roofline per precision on 1 GB300; adjoint/forward cost ratio"
 SEED = 5
+# the CUDA kernel behind each step-kernel choice of the library
+KERNEL_NAMES = {"fused": "k_step_fused", "fused_staged": "k_step_staged", "generic": "k_phi+k_mu+k_collide"}
 
 
 def parse_args():
@@ -55,6 +57,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-per-size", action="store_true",
+                    help="skip the FP32 line at 256^3 (the size of the FP32 roofline target)")
     ap.add_argument("--stencil", type=int, default=7, choices=[7, 19],
                     help="order-parameter stencils: 7-point (default) or 19-point isotropic")
     return ap.parse_args()
@@ -120,6 +124,32 @@ def recorded_fp64_ops():
             if len(parts) >= 4 and parts[0] == "generic" and parts[1] == "fp64" and parts[3] == want:
                 return float(parts[2])
     return None
+
+
+def fp64_pipe_probe(torch, ld, reps=5):
+    """Measured FP64 instruction rate of this GPU (the library's throughput
+    probe: 8 independent chains of one FP64 operation per thread, full
+    occupancy), best of `reps` timed launches per operation, in G
+    instructions/s; the roof of the FP64 step, which the FP64 pipe bounds."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks, iters = 8 * sms, 4096
+    sink = torch.zeros(blocks, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    rates = {}
+    for op, name in ((0, "dfma"), (1, "dadd"), (2, "dmul")):
+        for _ in range(2):
+            ld.ld_probe_fp64_rate(op, blocks, iters, sink, stream.cuda_stream)
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ld.ld_probe_fp64_rate(op, blocks, iters, sink, stream.cuda_stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        rates[name] = blocks * 256 * 8 * iters / (best * 1e-3) / 1e9
+    return rates
 
 
 def copy_probe_gbs(torch, nbytes=2 << 30, reps=10):
@@ -254,11 +284,12 @@ def max_over_ranks(world, value):
     return float(t.item())
 
 
-def time_precision(args, ld, phi_dev, precision, world, sample_clocks=False):
-    """Warm up, then time exactly args.steps steps (plus the final totals)."""
+def time_precision(args, ld, phi_dev, precision, world, sample_clocks=False, n=None):
+    """Warm up, then time exactly args.steps steps (plus the final totals) on
+    an n^3 lattice (the bench lattice unless given)."""
     import torch
 
-    n = args.size
+    n = args.size if n is None else n
     stream = torch.cuda.current_stream()
     sim = ld.LdSim(n, n, n, precision=precision, stream=stream.cuda_stream, stencil=args.stencil)
     sim.init(phi_dev)
@@ -287,13 +318,13 @@ def time_precision(args, ld, phi_dev, precision, world, sample_clocks=False):
     region_ms = region0.elapsed_time(region1)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     tot = totals.cpu().numpy()
-    fused = bool(ld.lib() and sim.params.kernel in (0, 2))
+    kernel = ld.ld_step_kernel(sim.ctx)
     sim.close()
     del sim
     torch.cuda.empty_cache()
     return {"region_ms": region_ms, "kernel_ms_mean": float(np.mean(step_ms)),
             "kernel_ms_median": float(np.median(step_ms)), "totals": tot.tolist(), "clocks": clocks,
-            "fused": fused}
+            "kernel": kernel}
 
 
 def time_e2e(args, ld, phi_host_pinned, precision):
@@ -472,6 +503,7 @@ def main():
         sites = n ** 3
         bps = VALUES_PER_SITE * BYTES_PER_VALUE[prec]
         results[prec] = {
+            "kernel": r["kernel"],
             "mlups": world * sites * args.steps / (region_ms * 1e-3) / 1e6,
             "ms_per_step": region_ms / args.steps,
             "kernel_ms": kernel_ms,
@@ -484,19 +516,41 @@ def main():
 
     primary = precisions[0]
     P = results[primary]
+    # The FP32 fused step's roofline target is stated at 256^3: time that
+    # lattice too (same seed, same steps), beside the bench lattice.
+    per_size = {}
+    if not args.no_per_size and n != 256 and "fp32" in results:
+        n2 = 256
+        phi2 = torch.from_numpy(inputs.spinodal_phi(n2, n2, n2, seed=SEED)).to("cuda")
+        r2 = time_precision(args, ld, phi2, "fp32", world, n=n2)
+        del phi2
+        reg2 = max_over_ranks(world, r2["region_ms"])
+        k2 = max_over_ranks(world, r2["kernel_ms_mean"])
+        bps = VALUES_PER_SITE * BYTES_PER_VALUE["fp32"]
+        gbs = n2 ** 3 * bps / (k2 * 1e-3) / 1e9
+        per_size[str(n2)] = {"precision": "fp32", "sites": n2 ** 3, "steps": args.steps,
+                             "mlups": world * n2 ** 3 * args.steps / (reg2 * 1e-3) / 1e6,
+                             "ms_per_step": reg2 / args.steps, "kernel_ms": k2, "algorithmic_gbs": gbs,
+                             "roofline_frac": gbs / peak, "kernel": r2["kernel"]}
     if "fp64" in results:
-        # FP64 is bounded by the FP64 pipe: 2 FP64 instructions per clock per SM
-        # (GB300: 1.25 TFLOP/s nominal FP64 with an FMA counted as 2 flops, at
-        # 152 SMs x 2.07 GHz), times the SMs and the maximum SM clock seen.
+        # FP64 is bounded by the FP64 pipe. Its roof is the FP64 instruction
+        # rate measured on this GPU by the library's probe (the best of DFMA,
+        # DADD and DMUL); the nominal figure (2 FP64 instructions per clock
+        # per SM: 1.25 TFLOP/s with an FMA counted as 2 flops at 152 SMs x
+        # 2.07 GHz) is reported beside it.
         ops = recorded_fp64_ops() if args.stencil == 7 else None  # the record is for the default stencils
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         mhz = (P["clocks"] or {}).get("sm_max_mhz") or 2070.0
-        peak_ops = 2.0 * sms * mhz * 1e6 / 1e9
+        nominal = 2.0 * sms * mhz * 1e6 / 1e9
+        rates = fp64_pipe_probe(torch, ld)
+        peak_ops = max(rates.values())
         R64 = results["fp64"]
         achieved = None if ops is None else R64["mlups"] * 1e6 * ops / 1e9
         R64["alu"] = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "G FP64 inst/s",
                       "frac": None if achieved is None else achieved / peak_ops, "fp64_inst_per_site": ops,
-                      "peak_source": f"derived: 2 FP64 inst/clk/SM x {sms} SMs x {mhz:.0f} MHz"}
+                      "peak_source": "measured: ld_probe_fp64_rate, best of DFMA/DADD/DMUL chains",
+                      "probe_rates": rates, "nominal_peak": nominal,
+                      "nominal_source": f"2 FP64 inst/clk/SM x {sms} SMs x {mhz:.0f} MHz"}
     probe = copy_probe_gbs(torch) if rank == 0 else None
     e2e = None
     if not args.no_e2e:
@@ -530,7 +584,7 @@ def main():
         "config": cfg,
         "roofline": {"bound": "hbm", "achieved": P["algorithmic_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": P["roofline_frac"], "traffic": traffic,
-                     "kernel": "k_step_fused", "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                     "kernel": KERNEL_NAMES.get(P["kernel"], P["kernel"]), "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
                      "per_site_bytes": P["bytes_per_site"], "kernel_ms": P["kernel_ms"],
                      "copy_probe_gbs": probe, "frac_of_copy_probe": None if not probe else P["algorithmic_gbs"] / probe},
@@ -539,6 +593,7 @@ def main():
         "gpu_launches": args.steps + 2,
         "cpu_baseline": cpu,
         "per_precision": {p: {k: v for k, v in r.items() if k not in ("clocks",)} for p, r in results.items()},
+        "per_size": per_size,
         "adjoint_forward_ratio": None if adj is None else adj["backward_ms_per_step"] / P["ms_per_step"],
         "adjoint": adj,
     }

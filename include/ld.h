@@ -61,13 +61,15 @@ enum { LD_FP64 = 0, LD_FP32 = 1, LD_FP16DEV = 2, LD_BF16DEV = 3 };
  * LD_KERNEL_FUSED: one launch per step that reads and writes each distribution
  *   once from HBM; phi and mu rings in shared memory, distributions through
  *   registers (nx % 32 == 0, ny % 8 == 0, nz % 4 == 0).
- * LD_KERNEL_FUSED_TMA: the fused step with each plane's distributions staged
- *   in shared memory by TMA bulk copies; FP32 and the 16-bit forms only
- *   (nx % 32 == 0, ny % 8 == 0, nz % 4 == 0).
+ * LD_KERNEL_FUSED_STAGED: the fused step with each plane's distributions
+ *   staged in shared memory one plane ahead by asynchronous 16-byte copies
+ *   (cp.async, completion tracked on mbarriers with bounded waits); FP32 and
+ *   the 16-bit forms only (nx % 32 == 0, ny % 8 == 0, nz % 4 == 0); every
+ *   stencil and rounding option of FUSED.
  * LD_KERNEL_AUTO: FUSED when the lattice admits it, else GENERIC; always
  * GENERIC for LD_FP64, which is bound by the FP64 pipe, where the generic
  * launches do less FP64 work per site (no halo phi sums). */
-enum { LD_KERNEL_AUTO = 0, LD_KERNEL_GENERIC = 1, LD_KERNEL_FUSED = 2, LD_KERNEL_FUSED_TMA = 3 };
+enum { LD_KERNEL_AUTO = 0, LD_KERNEL_GENERIC = 1, LD_KERNEL_FUSED = 2, LD_KERNEL_FUSED_STAGED = 3 };
 
 /* Stencils of the order-parameter gradients (mu's Laplacian, the force's
  * gradient of mu, the grad phi output). The paper names these kernels
@@ -75,8 +77,7 @@ enum { LD_KERNEL_AUTO = 0, LD_KERNEL_GENERIC = 1, LD_KERNEL_FUSED = 2, LD_KERNEL
  * LD_STENCIL_7: 7-point Laplacian and 2-point central difference (default).
  * LD_STENCIL_19: 19-point isotropic forms on the D3Q19 neighbourhood,
  *   lap h = sum_i 6 w_i (h(x + c_i) - h(x)), grad h = sum_i 3 w_i c_i h(x + c_i),
- *   whose leading truncation errors do not depend on direction; GENERIC and
- *   FUSED kernels only (LD_EINVAL with LD_KERNEL_FUSED_TMA). */
+ *   whose leading truncation errors do not depend on direction. */
 enum { LD_STENCIL_7 = 0, LD_STENCIL_19 = 1 };
 
 /* Form of the force on the fluid (the "Chemical stress" kernel of a Ludwig
@@ -87,7 +88,7 @@ enum { LD_STENCIL_7 = 0, LD_STENCIL_19 = 1 };
  *          + kappa d_a phi d_b phi,
  *   with the selected stencils; equal to -phi grad(mu) in the continuum, it
  *   conserves total momentum exactly on the lattice. GENERIC kernel only
- *   (AUTO picks it; FUSED and FUSED_TMA give LD_EINVAL); no adjoint
+ *   (AUTO picks it; FUSED and FUSED_STAGED give LD_EINVAL); no adjoint
  *   (ld_adjoint_workspace_bytes returns 0, ld_adjoint_attach LD_EINVAL).
  *   Fixed at ld_create (its 6 stress fields are part of the workspace). */
 enum { LD_FORCE_POTENTIAL = 0, LD_FORCE_STRESS = 1 };
@@ -100,7 +101,7 @@ enum { LD_FORCE_POTENTIAL = 0, LD_FORCE_STRESS = 1 };
  *   source, relax with omega+ = 1/tau_f and omega- = 1/tau-, where
  *   tau- = 1/2 + magic/(tau_f - 1/2); the source parts carry (1 - omega+/2)
  *   and (1 - omega-/2). The shear viscosity is still (tau_f - 1/2)/3.
- *   GENERIC kernel only (AUTO picks it; FUSED and FUSED_TMA give LD_EINVAL);
+ *   GENERIC kernel only (AUTO picks it; FUSED and FUSED_STAGED give LD_EINVAL);
  *   no adjoint. Fixed at ld_create. */
 enum { LD_COLLISION_BGK = 0, LD_COLLISION_TRT = 1 };
 
@@ -121,8 +122,8 @@ enum { LD_COLLISION_BGK = 0, LD_COLLISION_TRT = 1 };
  *   the SplitMix64 output of state seed + (c + 1)*gamma (mod 2^64) with
  *   c = ((2t + a)*5 + i/4)*N + s, and k is its bits 16*(i%4) .. 16*(i%4)+15
  *   (the value collided at site s in direction i). Fixed seed: bitwise
- *   reproducible runs. 16-bit forms only; not with LD_KERNEL_FUSED_TMA,
- *   ld_step_between or the adjoint (LD_EINVAL), whose recomputation would
+ *   reproducible runs. 16-bit forms only; not with ld_step_between or the
+ *   adjoint (LD_EINVAL), whose recomputation would
  *   need the step counter of the saved state. Fixed at ld_create. */
 enum { LD_ROUND_NEAREST = 0, LD_ROUND_STOCHASTIC = 1 };
 
@@ -139,7 +140,7 @@ typedef struct {
     double tau_f, tau_g;       /* relaxation times, each > 1/2 */
     double rho0;               /* reference density (default rho, f deviation reference) */
     int precision;             /* LD_FP64 .. LD_BF16DEV */
-    int kernel;                /* LD_KERNEL_AUTO / GENERIC / FUSED / FUSED_TMA */
+    int kernel;                /* LD_KERNEL_AUTO / GENERIC / FUSED / FUSED_STAGED */
     int stencil;               /* LD_STENCIL_7 / LD_STENCIL_19 */
     int force;                 /* LD_FORCE_POTENTIAL / LD_FORCE_STRESS */
     int collision;             /* LD_COLLISION_BGK / LD_COLLISION_TRT */
@@ -180,6 +181,41 @@ int ld_set_params(ld_ctx* ctx, const ld_params* p);
  * and sets the step counter t of stochastic rounding to 0. */
 int ld_init(ld_ctx* ctx, const double* phi, const double* rho, const double* u);
 
+/* ld_init for a lattice that is one part of a larger one (a slab of a
+ * domain decomposition): the 16-bit storage forms take their g deviation
+ * reference from phi_mean, the mean phi of the whole lattice, instead of the
+ * mean of this part's phi, so that every part stores deviations from the
+ * same reference as the whole lattice would. Otherwise as ld_init (the
+ * reference has no effect on FP64 and FP32). LD_EINVAL for a non-finite
+ * phi_mean. */
+int ld_init_with_reference(ld_ctx* ctx, const double* phi, const double* rho, const double* u, double phi_mean);
+
+/* FP64 sum of a device double[n] (any n >= 1, independent of the context's
+ * lattice) into device sum[0], in the fixed order ld_init sums phi for its
+ * mean: the whole lattice's mean phi for ld_init_with_reference, bit for bit
+ * the one ld_init of the whole lattice would take. Uses the context's
+ * reduction scratch; stream-ordered. */
+int ld_field_sum(ld_ctx* ctx, long long n, const double* x, double* sum);
+
+/* Halo exchange of a domain decomposition (the paper's Sec. 2.1.1: each
+ * sub-domain is surrounded by halo regions filled from its neighbours).
+ * ld_pack_planes copies the f and g of nplanes whole z-planes of the current
+ * state, starting at plane z0 (taken modulo nz, the range wrapping
+ * periodically), into dev_buf as [38][nplanes][ny][nx] values of the storage
+ * precision (f components 0..18, then g); ld_unpack_planes writes such a
+ * buffer into those planes. ld_planes_bytes gives the buffer size (0 for a
+ * NULL context or nplanes < 1). Stream-ordered device-to-device copies; the
+ * buffer is caller-owned device memory. LD_EINVAL for nplanes outside 1..nz
+ * or a host buffer; LD_ESTATE before the state is initialised. */
+size_t ld_planes_bytes(const ld_ctx* ctx, int nplanes);
+int ld_pack_planes(ld_ctx* ctx, int z0, int nplanes, void* dev_buf);
+int ld_unpack_planes(ld_ctx* ctx, int z0, int nplanes, const void* dev_buf);
+
+/* The step kernel a context runs (LD_KERNEL_AUTO resolved for its lattice,
+ * precision and options): LD_KERNEL_GENERIC, LD_KERNEL_FUSED or
+ * LD_KERNEL_FUSED_STAGED; LD_EINVAL for a NULL context. */
+int ld_step_kernel(const ld_ctx* ctx);
+
 /* Advance nsteps >= 0 full timesteps (moments, phi stencil and mu, force,
  * collisions of f and g, propagation). Each step adds 1 to the step counter
  * of stochastic rounding. Asynchronous. */
@@ -194,9 +230,19 @@ int ld_moments(ld_ctx* ctx, double* rho, double* u, double* phi, double* grad_ph
 
 /* Synchronise the stream and return LD_ENONFINITE if the state holds a NaN
  * or Inf (tested through the FP64 totals), LD_ECUDA if a kernel recorded that
- * it gave up waiting for its shared-memory copies, else LD_OK. Blocks the
- * host. */
+ * it gave up waiting for its shared-memory copies (the steps since then are
+ * invalid; ld_init clears the record), else LD_OK. Blocks the host. */
 int ld_check(ld_ctx* ctx);
+
+/* Test setting of the failure detection of ld_check (the paper has no
+ * counterpart; it exercises the bounded waits of LD_KERNEL_FUSED_STAGED
+ * without faulting or hanging the GPU). max_polls (>= 1) bounds every
+ * barrier wait of the staged step kernel (default 2^24 polls). With probe
+ * != 0 each of its threads also waits once per step on a barrier that
+ * nothing arrives on, and no copy is tracked by: that wait gives up after
+ * max_polls polls and records the failure that ld_check then reports, while
+ * the step itself completes. LD_EINVAL for max_polls < 1. */
+int ld_test_bounded_wait(ld_ctx* ctx, int max_polls, int probe);
 
 /* Copy the current pre-collision distributions out as double[19][N] each
  * (decoded from the storage precision). Either pointer may be NULL. */
@@ -281,11 +327,30 @@ int ld_adjoint_set(ld_ctx* ctx, const double* fbar, const double* gbar);
  * callback: it allocates nothing, and keeps its partial sums in a fixed
  * static device array (160 KiB, held by every GPU that loads the library
  * until exit). Limit: N <= 67,108,864 sites (LD_EINVAL beyond). The first
- * call on a device looks up that array's address and should come before any
- * stream capture. Calls share the array: calls that overlap on the GPU race.
- * Summation order is fixed (bitwise reproducible). No context needed;
- * errors are read with ld_last_error(NULL). */
+ * call on a device looks up that array's address, with that device current,
+ * and caches it; make that first call before any stream capture. The cached
+ * address belongs to the device's primary context: after cudaDeviceReset on
+ * that device the call is invalid for the rest of the process. Calls share
+ * the array: calls that overlap on the GPU race. f and g must each hold at
+ * least 19*N doubles and totals 5; only the size limit is checked here, the
+ * extent of the buffers is the caller's to ensure. Summation order is fixed
+ * (bitwise reproducible). No context needed; errors are read with
+ * ld_last_error(NULL). */
 int ld_totals_static(int nx, int ny, int nz, const double* f, const double* g, double* totals, void* cuda_stream);
+
+/* FP64 throughput probe: the ceiling of the FP64 step, which is bound by
+ * the FP64 pipe, measured on the current GPU. The paper bounds each kernel
+ * by the platform's measured STREAM bandwidth and peak double-precision rate
+ * (Sec. 4, Table 1 and its roofline ridge points); this call supplies the
+ * second for this GPU. Launches `blocks` CTAs of 256 threads on
+ * cuda_stream, each thread running 8 independent chains of `iters` FP64
+ * operations: op 0 fused multiply-add, 1 add, 2 multiply (one instruction
+ * each). The caller times the launch (CUDA events) and divides
+ * blocks * 256 * 8 * iters by the time. sink: device double[blocks], never
+ * written in practice (it keeps the chains live). LD_EINVAL for op outside
+ * 0..2, blocks or iters < 1, or a host sink. Context-free; errors via
+ * ld_last_error(NULL). */
+int ld_probe_fp64_rate(int op, int blocks, int iters, double* sink, void* cuda_stream);
 
 /* Message for an error code, and the last error recorded on a context. */
 const char* ld_strerror(int code);

@@ -7,6 +7,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ld.h"
 #include "ld_internal.h"
 
@@ -82,26 +84,20 @@ bool params_ok(const ld_params* p, const char** why) {
     if (!isfinite(p->A) || !isfinite(p->B) || !isfinite(p->kappa) || !isfinite(p->Gamma))
         return *why = "A, B, kappa, Gamma must be finite", false;
     if (p->precision < LD_FP64 || p->precision > LD_BF16DEV) return *why = "unknown precision", false;
-    if (p->kernel < LD_KERNEL_AUTO || p->kernel > LD_KERNEL_FUSED_TMA) return *why = "unknown kernel", false;
+    if (p->kernel < LD_KERNEL_AUTO || p->kernel > LD_KERNEL_FUSED_STAGED) return *why = "unknown kernel", false;
     if (p->stencil != LD_STENCIL_7 && p->stencil != LD_STENCIL_19) return *why = "unknown stencil", false;
-    if (p->stencil == LD_STENCIL_19 && p->kernel == LD_KERNEL_FUSED_TMA)
-        return *why = "the TMA-staged kernel has the 7-point stencils only", false;
     if (p->force != LD_FORCE_POTENTIAL && p->force != LD_FORCE_STRESS) return *why = "unknown force form", false;
-    if (p->force == LD_FORCE_STRESS && (p->kernel == LD_KERNEL_FUSED || p->kernel == LD_KERNEL_FUSED_TMA))
+    if (p->force == LD_FORCE_STRESS && (p->kernel == LD_KERNEL_FUSED || p->kernel == LD_KERNEL_FUSED_STAGED))
         return *why = "the stress form of the force runs on the generic kernel only", false;
     if (p->collision != LD_COLLISION_BGK && p->collision != LD_COLLISION_TRT) return *why = "unknown collision", false;
     if (p->collision == LD_COLLISION_TRT) {
         if (!(p->magic > 0.0) || !isfinite(p->magic)) return *why = "the TRT magic parameter must be positive", false;
-        if (p->kernel == LD_KERNEL_FUSED || p->kernel == LD_KERNEL_FUSED_TMA)
+        if (p->kernel == LD_KERNEL_FUSED || p->kernel == LD_KERNEL_FUSED_STAGED)
             return *why = "the TRT collision runs on the generic kernel only", false;
     }
     if (p->rounding != LD_ROUND_NEAREST && p->rounding != LD_ROUND_STOCHASTIC) return *why = "unknown rounding", false;
-    if (p->rounding == LD_ROUND_STOCHASTIC) {
-        if (p->precision != LD_FP16DEV && p->precision != LD_BF16DEV)
-            return *why = "stochastic rounding applies to the 16-bit storage forms only", false;
-        if (p->kernel == LD_KERNEL_FUSED_TMA)
-            return *why = "the TMA-staged kernel rounds to nearest only", false;
-    }
+    if (p->rounding == LD_ROUND_STOCHASTIC && p->precision != LD_FP16DEV && p->precision != LD_BF16DEV)
+        return *why = "stochastic rounding applies to the 16-bit storage forms only", false;
     return true;
 }
 
@@ -172,7 +168,7 @@ int ld_create(int nx, int ny, int nz, const ld_params* p, void* dev_workspace, s
                                 : ld::choose_step_kernel(nx, ny, nz, p->precision, p->kernel);
     if (step_kernel == 0)
         return fail(nullptr, LD_EINVAL,
-                    "fused kernels need nx %% 32 == 0, ny %% 8 == 0, nz %% 4 == 0 (TMA: FP32/FP16DEV/BF16DEV only)");
+                    "fused kernels need nx %% 32 == 0, ny %% 8 == 0, nz %% 4 == 0 (staged: FP32/FP16DEV/BF16DEV only)");
 
     ld_ctx* c = (ld_ctx*)calloc(1, sizeof(ld_ctx));
     if (!c) return fail(nullptr, LD_EINVAL, "host allocation of the context failed");
@@ -199,6 +195,8 @@ int ld_create(int nx, int ny, int nz, const ld_params* p, void* dev_workspace, s
     c->totals = (double*)(c->ws + L.totals);
     c->ref = (float*)(c->ws + L.ref);
     c->status = (int*)(c->ws + L.status);
+    c->wait_polls = ld::kDefaultWaitPolls;
+    c->wait_probe = 0;
     c->stream = (cudaStream_t)cuda_stream;
     c->initialized = false;
     c->step_kernel = step_kernel;
@@ -245,28 +243,130 @@ int ld_set_params(ld_ctx* c, const ld_params* p) {
     return LD_OK;
 }
 
-int ld_init(ld_ctx* c, const double* phi, const double* rho, const double* u) {
+}  // extern "C"
+
+namespace {
+int init_common(ld_ctx* c, const double* phi, const double* rho, const double* u, const double* ref_mean,
+                const char* where) {
     if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
     if (!is_device_ptr(phi)) return fail(c, LD_EINVAL, "phi must be a device pointer");
     if (!opt_device(rho) || !opt_device(u)) return fail(c, LD_EINVAL, "rho and u must be device pointers or NULL");
+    if (ref_mean && !isfinite(*ref_mean)) return fail(c, LD_EINVAL, "the reference mean must be finite");
     c->cur = 0;
     c->sr_step = 0;
-    cudaError_t e = ld::launch_init(c, phi, rho, u);
-    if (e != cudaSuccess) return cuda_fail(c, e, "ld_init");
+    cudaError_t e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);  // a fresh state has no failed wait
+    if (e == cudaSuccess) e = ld::launch_init(c, phi, rho, u, ref_mean);
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
     c->initialized = true;
     return LD_OK;
+}
+
+// z-planes [z0, z0 + nplanes) of the current state as at most two runs of
+// whole planes that do not wrap: (first plane, count) pairs.
+int plane_runs(const ld_ctx* c, int z0, int nplanes, int run_z[2], int run_n[2]) {
+    const int nz = c->geom.nz;
+    const int z = ((z0 % nz) + nz) % nz;
+    run_z[0] = z;
+    run_n[0] = nplanes <= nz - z ? nplanes : nz - z;
+    run_z[1] = 0;
+    run_n[1] = nplanes - run_n[0];
+    return run_n[1] > 0 ? 2 : 1;
+}
+
+// Copy whole planes between the current state (38 components, pitch npad)
+// and a packed buffer [38][nplanes][ny][nx] in the storage precision.
+int copy_planes(ld_ctx* c, int z0, int nplanes, void* buf, bool pack, const char* where) {
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (nplanes < 1 || nplanes > c->geom.nz) return fail(c, LD_EINVAL, "%s: nplanes must be in 1..nz", where);
+    if (!is_device_ptr(buf)) return fail(c, LD_EINVAL, "%s: the buffer must be a device pointer", where);
+    const size_t S = c->store_bytes;
+    const size_t plane_bytes = (size_t)c->geom.nx * c->geom.ny * S;
+    const size_t pitch_state = (size_t)c->geom.npad * S, pitch_buf = (size_t)nplanes * plane_bytes;
+    char* state = static_cast<char*>(c->dist[c->cur]);
+    int rz[2], rn[2];
+    const int runs = plane_runs(c, z0, nplanes, rz, rn);
+    size_t done = 0;
+    for (int r = 0; r < runs; ++r) {
+        char* st = state + (size_t)rz[r] * plane_bytes;
+        char* bf = static_cast<char*>(buf) + done;
+        const size_t width = (size_t)rn[r] * plane_bytes;
+        const cudaError_t e = pack ? cudaMemcpy2DAsync(bf, pitch_buf, st, pitch_state, width, 2 * kQ,
+                                                       cudaMemcpyDeviceToDevice, c->stream)
+                                   : cudaMemcpy2DAsync(st, pitch_state, bf, pitch_buf, width, 2 * kQ,
+                                                       cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, where);
+        done += width;
+    }
+    return LD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int ld_init(ld_ctx* c, const double* phi, const double* rho, const double* u) {
+    return init_common(c, phi, rho, u, nullptr, "ld_init");
+}
+
+int ld_init_with_reference(ld_ctx* c, const double* phi, const double* rho, const double* u, double phi_mean) {
+    return init_common(c, phi, rho, u, &phi_mean, "ld_init_with_reference");
+}
+
+int ld_field_sum(ld_ctx* c, long long n, const double* x, double* sum) {
+    if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
+    if (n < 1) return fail(c, LD_EINVAL, "n must be >= 1");
+    if (!is_device_ptr(x) || !is_device_ptr(sum)) return fail(c, LD_EINVAL, "x and sum must be device pointers");
+    const cudaError_t e = ld::launch_field_sum(c, n, x, sum);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ld_field_sum");
+    return LD_OK;
+}
+
+size_t ld_planes_bytes(const ld_ctx* c, int nplanes) {
+    if (!c || nplanes < 1) return 0;
+    return 2 * kQ * (size_t)nplanes * c->geom.nx * c->geom.ny * c->store_bytes;
+}
+
+int ld_pack_planes(ld_ctx* c, int z0, int nplanes, void* dev_buf) {
+    return copy_planes(c, z0, nplanes, dev_buf, true, "ld_pack_planes");
+}
+
+int ld_unpack_planes(ld_ctx* c, int z0, int nplanes, const void* dev_buf) {
+    return copy_planes(c, z0, nplanes, const_cast<void*>(dev_buf), false, "ld_unpack_planes");
 }
 
 int ld_step(ld_ctx* c, int nsteps) {
     int rc = check_ready(c);
     if (rc) return rc;
     if (nsteps < 0) return fail(c, LD_EINVAL, "nsteps must be >= 0");
+    nvtxRangePushA("ld_step");
     for (int t = 0; t < nsteps; ++t) {
         cudaError_t e = ld::launch_step(c, c->dist[c->cur], c->dist[1 - c->cur]);
-        if (e != cudaSuccess) return cuda_fail(c, e, "ld_step");
+        if (e != cudaSuccess) {
+            nvtxRangePop();
+            return cuda_fail(c, e, "ld_step");
+        }
         c->cur ^= 1;
         ++c->sr_step;
     }
+    nvtxRangePop();
+    return LD_OK;
+}
+
+int ld_step_kernel(const ld_ctx* c) {
+    if (!c) return LD_EINVAL;
+    switch (c->step_kernel) {
+        case ld::kStepGeneric: return LD_KERNEL_GENERIC;
+        case ld::kStepRegs: return LD_KERNEL_FUSED;
+        case ld::kStepStaged: return LD_KERNEL_FUSED_STAGED;
+        default: return LD_EINVAL;
+    }
+}
+
+int ld_test_bounded_wait(ld_ctx* c, int max_polls, int probe) {
+    if (!c) return fail(nullptr, LD_EINVAL, "context is NULL");
+    if (max_polls < 1) return fail(c, LD_EINVAL, "max_polls must be >= 1");
+    c->wait_polls = max_polls;
+    c->wait_probe = probe ? 1 : 0;
     return LD_OK;
 }
 

@@ -1,7 +1,8 @@
-// Inline-PTX helpers for the TMA bulk-copy pipeline: shared-memory mbarriers
-// and cp.async.bulk (global -> shared, completion counted in bytes on an
-// mbarrier). Every wait is bounded: on timeout the kernel records an error
-// in a device status word instead of spinning forever.
+// Inline-PTX helpers for asynchronous staging into shared memory:
+// shared-memory mbarriers, 16-byte cp.async copies whose completion a
+// barrier tracks, and global loads with L2 cache policies. Every wait is
+// bounded: on timeout the kernel records an error in a device status word
+// instead of spinning forever.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -13,11 +14,6 @@ namespace ld {
 // Status bits written by kernels into the workspace status word.
 constexpr int kStatusWaitTimeout = 1;
 
-// Upper bound on try_wait polls before a wait is declared failed. Each poll
-// returns after at most a short hardware-defined suspension, so this bounds
-// a wait to well under a few seconds.
-constexpr int kMaxWaitPolls = 1 << 24;
-
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -26,40 +22,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
-// Make mbarrier initialisation visible to the async (copy-engine) proxy.
+// Make mbarrier initialisation visible to the asynchronous copy units.
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// Order this thread's earlier shared-memory accesses before later async-proxy
-// writes into the same buffers.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Arrive once on the barrier and add `bytes` to the transaction count the
-// current phase waits for.
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
-// global to this CTA's shared memory; completes `bytes` on the barrier.
-__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-
-// The same copy with an L2 cache policy (from make_l2_evict_last_policy).
-__device__ __forceinline__ void bulk_copy_g2s_hint(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar,
-                                                   uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
-            "r"(dst),
-        "l"(src), "r"(bytes), "r"(bar), "l"(policy)
-        : "memory");
 }
 
 // L2 policy that keeps the copied lines resident in preference to others.
@@ -131,12 +96,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Wait for the phase with the given parity to complete; false (and the
-// status bit set) if it did not within kMaxWaitPolls polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int* status) {
-    for (int it = 0; it < kMaxWaitPolls; ++it)
+// status bit set) if it did not within max_polls polls.
+__device__ __forceinline__ bool mbar_wait_bounded_n(uint32_t bar, uint32_t parity, int* status, int max_polls) {
+    for (int it = 0; it < max_polls; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     atomicOr(status, kStatusWaitTimeout);
     return false;
 }
+
+// 16-byte copy global -> this CTA's shared memory (cp.async, cached in L2
+// only) with an L2 policy. Both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint64_t policy) {
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "l"(policy)
+                 : "memory");
+}
+
+// Arrive once on the barrier when all of this thread's earlier cp.async
+// copies have landed, without raising the phase's expected count (the
+// barrier is initialised with the number of threads that arrive this way).
+__device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Block until every cp.async copy this thread issued has landed.
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 }  // namespace ld

@@ -324,8 +324,9 @@ __device__ __forceinline__ void collide_f(R (&f)[Q], R rho, R ux, R uy, R uz, R 
     f[0] = f[0] - m.omega_f * (f[0] - feq0) + src0;
 }
 
-// FP64 on opposite pairs too (about 20 % fewer FP64 operations per site than
-// direction by direction, where the FP64 pipe is the bound); the rest
+// FP64 on opposite pairs too (with the g collision's pair form, about 35 %
+// fewer FP64 operations per site than direction by direction, where the FP64
+// pipe is the bound); the rest
 // equilibrium from its formula, the FP64 weights summing to 1 within an ulp.
 template <>
 __device__ __forceinline__ void collide_f<double>(double (&f)[Q], double rho, double ux, double uy, double uz,
@@ -381,6 +382,131 @@ __device__ __forceinline__ void collide_f<float>(float (&f)[Q], float rho, float
     const float feq0 = rho - 2.0f * moving;
     const float src0 = m.force_pre * wgt<float>(0) * (-3.0f * uF);
     f[0] = keep * f[0] + (m.omega_f * feq0 + src0);
+}
+
+// ---------------------------------------------------------------------------
+// Arithmetic in deviation space (the 16-bit storage forms).
+//
+// The stored values are h_i = f_i - r_i and h_i = g_i - q_i with fixed
+// references r_i (~ w_i rho0) and q_i (~ geq_i(phibar, 0, mubar)). A collision
+// written on the deviations needs no decode of the form r_i + h_i and no
+// encode of the form f_i - r_i: with R = sum r_i and delta = sum h_i,
+//   rho = R + delta,  j = sum_i c_i h_i  (r_i = r_-i, so the references cancel)
+//   f*_i - r_i = (1 - w_f) h_i + w_f (feq_i - r_i) + S_i,
+//   feq_i - r_i = w_i delta + (w_i R - r_i) + w_i rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u),
+// and with Phi = sum q_i, psi = sum h_i (phi = Phi + psi), dhat any constant,
+//   g*_i - q_i = (1 - w_g) h_i + w_g (geq_i - q_i),
+//   geq_i - q_i = w_i [psi - 3/2 phi u.u + 9/2 (dev - dhat)(|c_i|^2 - 1) + 3 phi c.u
+//                      + 9/2 phi (c.u)^2] + (w_i (Phi + 9/2 dhat (|c_i|^2 - 1)) - q_i),
+// dev = Gamma mu - phi/3. Both are the same step as collide_f / collide_g in
+// exact arithmetic; the constant terms in parentheses (a few units in the
+// last place of the references) are formed once, in FP64. The rest values
+// come by difference, so sum_i h*_i equals the conserved delta (f, plus the
+// Guo source's rounding) and psi (g) exactly as in collide_f / collide_g.
+struct DevRefs {
+    float R;      // sum_i r_i
+    float ef[3];  // w_i R - r_i for the rest, axis and diagonal directions
+    float Phi;    // sum_i q_i
+    float muP;    // A Phi + B Phi^3
+    float dhat;   // Gamma muP - Phi/3
+    float eg[3];  // w_i (Phi + 9/2 dhat (|c_i|^2 - 1)) - q_i per class
+};
+
+// Class of a direction: 0 rest, 1 axis, 2 diagonal.
+__host__ __device__ constexpr int dir_class(int i) { return i == 0 ? 0 : (i <= 6 ? 1 : 2); }
+
+// The constants from the 38 stored references (f then g), in FP64.
+__device__ inline DevRefs dev_refs_of(const float* ref, const Model<float>& m) {
+    double R = 0.0, Phi = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        R += (double)ref[i];
+        Phi += (double)ref[Q + i];
+    }
+    const double muP = (double)m.A * Phi + (double)m.B * Phi * Phi * Phi;
+    const double dhat = (double)m.Gamma * muP - Phi / 3.0;
+    DevRefs d;
+    d.R = (float)R;
+    d.Phi = (float)Phi;
+    d.muP = (float)muP;
+    d.dhat = (float)dhat;
+    const int rep[3] = {0, 1, 7};
+    for (int k = 0; k < 3; ++k) {
+        const int i = rep[k];
+        d.ef[k] = (float)(wgt<double>(i) * R - (double)ref[i]);
+        d.eg[k] = (float)(wgt<double>(i) * (Phi + 4.5 * dhat * (c2(i) - 1)) - (double)ref[Q + i]);
+    }
+    return d;
+}
+
+// BGK + Guo collision of the f deviations in place; delta = sum_i h_i,
+// rho = R + delta.
+__device__ __forceinline__ void collide_f_dev(float (&h)[Q], float delta, float rho, float ux, float uy, float uz,
+                                              float Fx, float Fy, float Fz, const Model<float>& m, const DevRefs& d) {
+    const float uu = ux * ux + uy * uy + uz * uz;
+    const float uF = ux * Fx + uy * Fy + uz * Fz;
+    const float keep = 1.0f - m.omega_f;
+    float moving = 0.0f;  // sum of the symmetric parts of feq_i - r_i over the pairs
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float w = wgt<float>(i);
+        const float wr = w * rho, pw = m.force_pre * w;
+        const float cu = cdot(i, ux, uy, uz);
+        const float cF = cdot(i, Fx, Fy, Fz);
+        const float eq_sym = w * delta + d.ef[dir_class(i)] + wr * (4.5f * cu * cu - 1.5f * uu);
+        const float eq_anti = 3.0f * wr * cu;
+        const float src_sym = pw * (9.0f * cu * cF - 3.0f * uF);
+        const float src_anti = 3.0f * pw * cF;
+        const float sym = m.omega_f * eq_sym + src_sym;
+        const float anti = m.omega_f * eq_anti + src_anti;
+        h[i] = keep * h[i] + (sym + anti);
+        h[i + 1] = keep * h[i + 1] + (sym - anti);
+        moving += eq_sym;
+    }
+    const float eq0 = delta - 2.0f * moving;
+    const float src0 = m.force_pre * wgt<float>(0) * (-3.0f * uF);
+    h[0] = keep * h[0] + (m.omega_f * eq0 + src0);
+}
+
+// BGK collision of the g deviations in place; psi = sum_i h_i, phi = Phi + psi,
+// dmu = mu - muP.
+__device__ __forceinline__ void collide_g_dev(float (&h)[Q], float psi, float phi, float dmu, float ux, float uy,
+                                              float uz, const Model<float>& m, const DevRefs& d) {
+    const float uu = ux * ux + uy * uy + uz * uz;
+    const float ddev = m.Gamma * dmu - psi / 3.0f;  // dev - dhat
+    const float base = psi - 1.5f * phi * uu;
+    const float keep = 1.0f - m.omega_g;
+    float moving = 0.0f;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float w = wgt<float>(i);
+        const float cu = cdot(i, ux, uy, uz);
+        const float eq_sym = w * (base + 4.5f * ddev * float(c2(i) - 1) + 4.5f * phi * cu * cu) + d.eg[dir_class(i)];
+        const float eq_anti = 3.0f * w * phi * cu;
+        const float sym = m.omega_g * eq_sym, anti = m.omega_g * eq_anti;
+        h[i] = keep * h[i] + (sym + anti);
+        h[i + 1] = keep * h[i + 1] + (sym - anti);
+        moving += eq_sym;
+    }
+    const float eq0 = psi - 2.0f * moving;
+    h[0] = keep * h[0] + m.omega_g * eq0;
+}
+
+// A stored value as float (exact for every storage type of the FP32 arithmetic).
+__device__ __forceinline__ float to_float(float v) { return v; }
+__device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// acc + (a 16-bit value), rounded once: the value converts exactly, so this
+// equals float(v) + acc; one instruction instead of a conversion and an add.
+__device__ __forceinline__ float add_f16(float acc, unsigned short bits) {
+    float r;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(r) : "h"(bits), "f"(acc));
+    return r;
+}
+__device__ __forceinline__ float add_bf16(float acc, unsigned short bits) {
+    float r;
+    asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(r) : "h"(bits), "f"(acc));
+    return r;
 }
 
 // Two-relaxation-time collision of f in place (LD_COLLISION_TRT). Each

@@ -26,7 +26,7 @@
 #pragma once
 #include "ld_common.cuh"
 #include "ld_internal.h"
-#include "ld_tma.cuh"
+#include "ld_async.cuh"
 
 namespace ld {
 namespace {
@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     __shared__ R phis[3][PH][PW];
     __shared__ R mus[3][MH][MW];
     __shared__ float refs[2 * Q];
+    __shared__ DevRefs dref;  // deviation-space constants (16-bit forms)
     extern __shared__ __align__(16) unsigned char keep_smem[];
     S* gring = reinterpret_cast<S*>(keep_smem);  // [3][Q][TY][kTX], slot = phi slot of the plane
 
@@ -85,6 +86,9 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     const int plane = nx * ny;
     const I npad = (I)g.npad;
     if (tid < 2 * Q) refs[tid] = ref_g[tid];
+    if constexpr (kKeepG) {
+        if (tid == 0) dref = dev_refs_of(ref_g, m);
+    }
     // g is read by the phi pass and, two planes later, by the collision:
     // keep those lines in L2 until then, and release them at the second read.
     const uint64_t keep_l2 = make_l2_evict_last_policy(), drop_l2 = make_l2_evict_first_policy();
@@ -113,10 +117,15 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
                         const float2 v = ld_l2_hint_pair(gs + i * npad + s, keep_l2);
                         a0 += v.x;
                         a1 += v.y;
-                    } else {
+                    } else {  // psi: the sum of the deviations
                         const unsigned v = ld_l2_hint_pair(gs + i * npad + s, keep_l2);
-                        a0 += Prec<P>::decode(bits16<S>(v & 0xffffu), refs[Q + i]);
-                        a1 += Prec<P>::decode(bits16<S>(v >> 16), refs[Q + i]);
+                        if constexpr (P == LD_FP16DEV) {
+                            a0 = add_f16(a0, (unsigned short)(v & 0xffffu));
+                            a1 = add_f16(a1, (unsigned short)(v >> 16));
+                        } else {
+                            a0 = add_bf16(a0, (unsigned short)(v & 0xffffu));
+                            a1 = add_bf16(a1, (unsigned short)(v >> 16));
+                        }
                         if (interior) *reinterpret_cast<unsigned*>(keep + i * (TY * kTX)) = v;
                     }
                 }
@@ -142,18 +151,26 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
         }
     };
     // mu over the tile + 1-halo from three phi slots (below, middle, above).
+    // The ring holds phi, or psi = phi - Phi in the 16-bit forms: the
+    // Laplacian is the same, the cubic term takes phi.
     auto mu_plane = [&](int slot, int lo, int mid, int hi) {
         for (int idx = tid; idx < MW * MH; idx += NT) {
             const int mx = idx % MW, my = idx / MW;
             const int hx = mx + 1, hy = my + 1;
+            const R c = phis[mid][hy][hx];
+            R lap;
             if constexpr (ISO) {
                 auto nb = [&](int i) { return phis[cz(i) > 0 ? hi : (cz(i) < 0 ? lo : mid)][hy + cy(i)][hx + cx(i)]; };
-                mus[slot][my][mx] = chem_potential_lap(phis[mid][hy][hx], lap19(phis[mid][hy][hx], nb), m);
+                lap = lap19(c, nb);
             } else {
                 const R nb = phis[mid][hy][hx + 1] + phis[mid][hy][hx - 1] + phis[mid][hy + 1][hx]
                            + phis[mid][hy - 1][hx] + phis[hi][hy][hx] + phis[lo][hy][hx];
-                mus[slot][my][mx] = chem_potential(phis[mid][hy][hx], nb, m);
+                lap = sub_rn(nb, mul_rn(R(6), c));
             }
+            if constexpr (kKeepG)
+                mus[slot][my][mx] = chem_potential_lap(dref.Phi + c, lap, m);
+            else
+                mus[slot][my][mx] = chem_potential_lap(c, lap, m);
         }
     };
     auto ps = [&](int zp) { return (zp - z0 + 2) % 3; };  // phi slot of plane zp (zp >= z0-2)
@@ -198,7 +215,12 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
         __syncthreads();
 
         const int ozp = z + 1 == nz ? (1 - nz) * plane : plane, ozm = z == 0 ? (nz - 1) * plane : -plane;
-        const R ph = phis[ps(k)][ty + 2][tx + 2];
+        const R ring_c = phis[ps(k)][ty + 2][tx + 2];  // phi, or psi in the 16-bit forms
+        R ph;
+        if constexpr (kKeepG)
+            ph = dref.Phi + ring_c;
+        else
+            ph = ring_c;
         const int mc = ms(k);
         const R muc = mus[mc][ty + 1][tx + 1];
         R gmx, gmy, gmz;
@@ -216,47 +238,66 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
             phi_out[s] = ph;
             mu_out[s] = muc;
         }
-
-        R f[Q];
-        R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            f[i] = Prec<P>::decode(kKeepG ? fpre[i] : fs[i * npad + s], refs[i]);
-            rho += f[i];
-            add_c(i, f[i], jx, jy, jz);
-        }
-        R ux, uy, uz;
-        guo_velocity(rho, jx, jy, jz, Fx, Fy, Fz, ux, uy, uz);
-        collide_f(f, rho, ux, uy, uz, Fx, Fy, Fz, m);
         const unsigned long long sr_st = SR ? sr.base + (unsigned long long)s * kSrGamma : 0ull;
         unsigned long long sr_w = 0;
+        auto dest = [&](int i) {
+            return s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
+                   (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
+        };
+
+        R f[Q];
+        R ux, uy, uz;
+        if constexpr (kKeepG) {  // deviation space
+            R delta = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                f[i] = to_float(fpre[i]);
+                delta += f[i];
+                add_c(i, f[i], jx, jy, jz);
+            }
+            const R rho = dref.R + delta;
+            guo_velocity(rho, jx, jy, jz, Fx, Fy, Fz, ux, uy, uz);
+            collide_f_dev(f, delta, rho, ux, uy, uz, Fx, Fy, Fz, m, dref);
+        } else {
+            R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                f[i] = Prec<P>::decode(fs[i * npad + s], refs[i]);
+                rho += f[i];
+                add_c(i, f[i], jx, jy, jz);
+            }
+            guo_velocity(rho, jx, jy, jz, Fx, Fy, Fz, ux, uy, uz);
+            collide_f(f, rho, ux, uy, uz, Fx, Fy, Fz, m);
+        }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const int d = s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
-                          (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
+            const R ref = kKeepG ? R(0) : refs[i];  // deviations are stored as they are
             if constexpr (SR)
-                __stcs(fd + i * npad + d, Prec<P>::encode_sr(f[i], refs[i], sr_key(sr, sr_st, 0, i, sr_w)));
+                __stcs(fd + i * npad + dest(i), Prec<P>::encode_sr(f[i], ref, sr_key(sr, sr_st, 0, i, sr_w)));
             else
-                __stcs(fd + i * npad + d, Prec<P>::encode(f[i], refs[i]));
+                __stcs(fd + i * npad + dest(i), Prec<P>::encode(f[i], ref));
         }
 
         R gg[Q];
+        if constexpr (kKeepG) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const S v = kKeepG    ? gring[((size_t)ps(k) * Q + i) * (TY * kTX) + ty * kTX + tx]
-                        : kEarlyG ? gpre[i]
-                                  : ld_l2_hint(gs + i * npad + s, drop_l2);
-            gg[i] = Prec<P>::decode(v, refs[Q + i]);
+            for (int i = 0; i < Q; ++i) gg[i] = to_float(gring[((size_t)ps(k) * Q + i) * (TY * kTX) + ty * kTX + tx]);
+            collide_g_dev(gg, ring_c, ph, muc - dref.muP, ux, uy, uz, m, dref);
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const S v = kEarlyG ? gpre[i] : ld_l2_hint(gs + i * npad + s, drop_l2);
+                gg[i] = Prec<P>::decode(v, refs[Q + i]);
+            }
+            collide_g(gg, ph, muc, ux, uy, uz, m);
         }
-        collide_g(gg, ph, muc, ux, uy, uz, m);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const int d = s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
-                          (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
+            const R ref = kKeepG ? R(0) : refs[Q + i];
             if constexpr (SR)
-                __stcs(gd + i * npad + d, Prec<P>::encode_sr(gg[i], refs[Q + i], sr_key(sr, sr_st, 1, i, sr_w)));
+                __stcs(gd + i * npad + dest(i), Prec<P>::encode_sr(gg[i], ref, sr_key(sr, sr_st, 1, i, sr_w)));
             else
-                __stcs(gd + i * npad + d, Prec<P>::encode(gg[i], refs[Q + i]));
+                __stcs(gd + i * npad + dest(i), Prec<P>::encode(gg[i], ref));
         }
     }
 }
@@ -289,13 +330,8 @@ cudaError_t launch_fused(ld_ctx* c, const void* src, void* dst, void* fields) {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     constexpr size_t kRingBytes = sizeof(S) == 2 ? 3 * (size_t)Q * kTY * kTX * sizeof(S) : 0;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_fused<P, kTY, I, ISO, SR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kRingBytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = set_max_dynamic_smem_once<k_step_fused<P, kTY, I, ISO, SR>>((int)kRingBytes);
+    if (e != cudaSuccess) return e;
     const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
     const int zc = choose_zc(g.nx, g.ny, g.nz, c->num_sms, fused_ctas_per_sm<P>());
     const dim3 grid(g.nx / kTX, g.ny / kTY, g.nz / zc);

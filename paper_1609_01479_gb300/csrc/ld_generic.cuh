@@ -312,11 +312,14 @@ __global__ void __launch_bounds__(kThreads)
 
 // Deviation references from the total of phi (in totals[0]): f_i: w_i rho0;
 // g_i: geq_i(phibar, 0, A phibar + B phibar^3).
-__global__ void k_refs(const double* __restrict__ totals, long long n, Model<double> m, double rho0,
-                       float* __restrict__ ref) {
+// Deviation references of the 16-bit forms: f_i w_i rho0; g_i geq_i(pb, 0, mu(pb))
+// with pb the mean of the initial phi: totals[0] / n (mean_given = false) or
+// `mean` itself (a part of a larger lattice that takes the whole one's mean).
+__global__ void k_refs(const double* __restrict__ totals, long long n, double mean, int mean_given, Model<double> m,
+                       double rho0, float* __restrict__ ref) {
     const int i = threadIdx.x;
     if (i >= Q) return;
-    const double pb = totals[0] / (double)n;
+    const double pb = mean_given ? mean : totals[0] / (double)n;
     const double mub = m.A * pb + m.B * pb * pb * pb;
     ref[i] = (float)(wgt<double>(i) * rho0);
     ref[Q + i] = (float)(wgt<double>(i) * (pb + 4.5 * (m.Gamma * mub - pb / 3.0) * (c2(i) - 1)));
@@ -512,14 +515,17 @@ __global__ void __launch_bounds__(kThreads) k_propagate(Geom g, int reverse, con
 
 // ---------------------------------------------------------------------------
 template <int P>
-cudaError_t init_p(ld_ctx* c, const double* phi, const double* rho, const double* u) {
+cudaError_t init_p(ld_ctx* c, const double* phi, const double* rho, const double* u, const double* ref_mean) {
     using S = typename Prec<P>::store_t;
     const Geom g = to_dev(c->geom);
     const Model<double> m = model_of<double>(c->prm);
     if (Prec<P>::kDev) {
-        k_sum_field<<<kRedBlocks, kRedThreads, 0, c->stream>>>(g.n, phi, c->partials);
-        k_finalize<<<1, kRedBlocks, 0, c->stream>>>(c->partials, 1, c->totals);
-        k_refs<<<1, 32, 0, c->stream>>>(c->totals, g.n, m, c->prm.rho0, c->ref);
+        if (!ref_mean) {
+            k_sum_field<<<kRedBlocks, kRedThreads, 0, c->stream>>>(g.n, phi, c->partials);
+            k_finalize<<<1, kRedBlocks, 0, c->stream>>>(c->partials, 1, c->totals);
+        }
+        k_refs<<<1, 32, 0, c->stream>>>(c->totals, g.n, ref_mean ? *ref_mean : 0.0, ref_mean ? 1 : 0, m, c->prm.rho0,
+                                        c->ref);
     } else {
         k_default_refs<<<1, 32, 0, c->stream>>>(c->prm.rho0, c->ref);
     }

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <atomic>
+
 #include "ld.h"
 
 namespace ld {
@@ -27,6 +29,11 @@ constexpr int kRedBlocks = 1024;
 constexpr int kRedThreads = 256;
 constexpr int kRedFields = 8;  // partial slots per block
 
+// Poll limit of a kernel's barrier waits (mbarrier try_wait polls). Each
+// poll returns after at most a short hardware-defined suspension, so this
+// bounds a wait to well under a few seconds.
+constexpr int kDefaultWaitPolls = 1 << 24;
+
 }  // namespace ld
 
 struct ld_ctx {
@@ -46,6 +53,8 @@ struct ld_ctx {
     double* totals;    // 8 doubles scratch
     float* ref;        // 38 floats: f then g deviation references
     int* status;       // device status word (kernel wait timeouts)
+    int wait_polls;    // poll limit of the staged kernel's barrier waits
+    int wait_probe;    // test setting: the staged kernel also waits on a barrier nothing arrives on
     cudaStream_t stream;
     bool initialized;
     int step_kernel;  // ld::StepKernel
@@ -89,7 +98,8 @@ inline void* g_of(const ld_ctx* c, int buf) { return g_part(c, c->dist[buf]); }
 // (ld_prec_lp.cu) lets the compiler contract.
 #define LD_PRECISION_LAUNCHERS(NS)                                                                \
     namespace NS {                                                                                \
-    cudaError_t init(ld_ctx* c, const double* phi, const double* rho, const double* u);          \
+    cudaError_t init(ld_ctx* c, const double* phi, const double* rho, const double* u,           \
+                     const double* ref_mean);                                                     \
     cudaError_t phi_mu(ld_ctx* c, const void* state);                                             \
     cudaError_t collide_generic(ld_ctx* c, const void* src, void* dst, void* fields);             \
     cudaError_t macros(ld_ctx* c, double* rho, double* u, double* phi, double* grad_phi);         \
@@ -97,13 +107,13 @@ inline void* g_of(const ld_ctx* c, int buf) { return g_part(c, c->dist[buf]); }
     cudaError_t decode(ld_ctx* c, double* f, double* g);                                          \
     cudaError_t encode(ld_ctx* c, const double* f, const double* g);                              \
     cudaError_t step_fused_regs(ld_ctx* c, const void* src, void* dst, void* fields);             \
-    cudaError_t step_tma(ld_ctx* c, const void* src, void* dst, void* fields);                    \
+    cudaError_t step_staged(ld_ctx* c, const void* src, void* dst, void* fields);                 \
     cudaError_t adj_step(ld_ctx* c, const void* state_t, const void* fields_t, double* grad);     \
     cudaError_t adj_seed(ld_ctx* c, const double* phibar);                                        \
     cudaError_t adj_init(ld_ctx* c, const double* phi0, const double* u0, double* gphi0, double* grad); \
     cudaError_t adj_io(ld_ctx* c, int to_double, double* fbar, double* gbar);                     \
     bool regs_supported(int nx, int ny, int nz);                                                  \
-    bool tma_supported(int nx, int ny, int nz, int prec);                                         \
+    bool staged_supported(int nx, int ny, int nz, int prec);                                      \
     }
 LD_PRECISION_LAUNCHERS(f64)
 LD_PRECISION_LAUNCHERS(lp)
@@ -111,17 +121,39 @@ LD_PRECISION_LAUNCHERS(lp)
 
 // Precision-independent (ld_prec_lp.cu).
 cudaError_t launch_propagate(ld_ctx* c, int reverse);
+// FP64 sum of a device double[n] into out[0], in the fixed order ld_init
+// uses for the mean of phi (the context's reduction scratch).
+cudaError_t launch_field_sum(ld_ctx* c, long long n, const double* x, double* out);
 cudaError_t launch_default_refs(ld_ctx* c);
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per device (the attribute belongs to the device's context).
+// Safe to call from several host threads: a repeated setting is harmless.
+template <auto Kernel>
+cudaError_t set_max_dynamic_smem_once(int bytes) {
+    static std::atomic<unsigned long long> done{0};  // bit d: set on device d (d < 64)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
+
 // Step kernels (ld_ctx::step_kernel).
-enum StepKernel { kStepGeneric = 1, kStepTma = 2, kStepRegs = 3 };
+enum StepKernel { kStepGeneric = 1, kStepStaged = 2, kStepRegs = 3 };
 // The kernel a request resolves to for this lattice and precision, or 0 if
 // the requested one cannot run it.
 int choose_step_kernel(int nx, int ny, int nz, int prec, int requested);
 
 inline bool is_f64(const ld_ctx* c) { return c->prec == LD_FP64; }
-inline cudaError_t launch_init(ld_ctx* c, const double* phi, const double* rho, const double* u) {
-    return is_f64(c) ? f64::init(c, phi, rho, u) : lp::init(c, phi, rho, u);
+// ref_mean: host pointer to the mean phi the 16-bit forms' g references are
+// taken from, or null for the mean of the given phi.
+inline cudaError_t launch_init(ld_ctx* c, const double* phi, const double* rho, const double* u,
+                               const double* ref_mean = nullptr) {
+    return is_f64(c) ? f64::init(c, phi, rho, u, ref_mean) : lp::init(c, phi, rho, u, ref_mean);
 }
 inline cudaError_t launch_phi_mu(ld_ctx* c, const void* state) {
     return is_f64(c) ? f64::phi_mu(c, state) : lp::phi_mu(c, state);
@@ -156,8 +188,8 @@ inline cudaError_t launch_adj_io(ld_ctx* c, int to_double, double* fbar, double*
 inline cudaError_t launch_step(ld_ctx* c, const void* src, void* dst, void* fields = nullptr) {
     if (c->step_kernel == kStepGeneric)
         return is_f64(c) ? f64::collide_generic(c, src, dst, fields) : lp::collide_generic(c, src, dst, fields);
-    if (c->step_kernel == kStepTma)
-        return is_f64(c) ? f64::step_tma(c, src, dst, fields) : lp::step_tma(c, src, dst, fields);
+    if (c->step_kernel == kStepStaged)
+        return is_f64(c) ? f64::step_staged(c, src, dst, fields) : lp::step_staged(c, src, dst, fields);
     return is_f64(c) ? f64::step_fused_regs(c, src, dst, fields) : lp::step_fused_regs(c, src, dst, fields);
 }
 

@@ -2,7 +2,7 @@
 // kernels, and the launches that do not depend on the precision.
 #include "ld_fused.cuh"
 #include "ld_generic.cuh"
-#include "ld_pipe.cuh"
+#include "ld_staged.cuh"
 #include "ld_adjoint.cuh"
 
 namespace ld {
@@ -16,8 +16,8 @@ namespace lp {
         default: return cudaErrorInvalidValue;               \
     }
 
-cudaError_t init(ld_ctx* c, const double* phi, const double* rho, const double* u) {
-    LD_LP_DISPATCH(init_p, c, phi, rho, u);
+cudaError_t init(ld_ctx* c, const double* phi, const double* rho, const double* u, const double* ref_mean) {
+    LD_LP_DISPATCH(init_p, c, phi, rho, u, ref_mean);
 }
 cudaError_t phi_mu(ld_ctx* c, const void* state) { LD_LP_DISPATCH(phi_mu_p, c, state); }
 cudaError_t collide_generic(ld_ctx* c, const void* src, void* dst, void* fields) {
@@ -32,8 +32,8 @@ cudaError_t encode(ld_ctx* c, const double* f, const double* g) { LD_LP_DISPATCH
 cudaError_t step_fused_regs(ld_ctx* c, const void* src, void* dst, void* fields) {
     LD_LP_DISPATCH(step_fused_p, c, src, dst, fields);
 }
-cudaError_t step_tma(ld_ctx* c, const void* src, void* dst, void* fields) {
-    LD_LP_DISPATCH(step_tma_p, c, src, dst, fields);
+cudaError_t step_staged(ld_ctx* c, const void* src, void* dst, void* fields) {
+    LD_LP_DISPATCH(step_staged_p, c, src, dst, fields);
 }
 bool regs_supported(int nx, int ny, int nz) { return fused_supported_impl(nx, ny, nz); }
 cudaError_t adj_step(ld_ctx* c, const void* st, const void* fields, double* grad) {
@@ -46,11 +46,11 @@ cudaError_t adj_init(ld_ctx* c, const double* phi0, const double* u0, double* gp
 cudaError_t adj_io(ld_ctx* c, int to_double, double* fbar, double* gbar) {
     LD_LP_DISPATCH(adj_io_p, c, to_double, fbar, gbar);
 }
-bool tma_supported(int nx, int ny, int nz, int prec) {
+bool staged_supported(int nx, int ny, int nz, int prec) {
     switch (prec) {
-        case LD_FP32: return pipe_supported_p<LD_FP32>(nx, ny, nz);
-        case LD_FP16DEV: return pipe_supported_p<LD_FP16DEV>(nx, ny, nz);
-        case LD_BF16DEV: return pipe_supported_p<LD_BF16DEV>(nx, ny, nz);
+        case LD_FP32: return staged_supported_p<LD_FP32>(nx, ny, nz);
+        case LD_FP16DEV: return staged_supported_p<LD_FP16DEV>(nx, ny, nz);
+        case LD_BF16DEV: return staged_supported_p<LD_BF16DEV>(nx, ny, nz);
         default: return false;
     }
 }
@@ -60,15 +60,20 @@ bool tma_supported(int nx, int ny, int nz, int prec) {
 }  // namespace lp
 
 cudaError_t launch_propagate(ld_ctx* c, int reverse) { return propagate_raw(c, reverse); }
+cudaError_t launch_field_sum(ld_ctx* c, long long n, const double* x, double* out) {
+    k_sum_field<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, x, c->partials);
+    k_finalize<<<1, kRedBlocks, 0, c->stream>>>(c->partials, 1, out);
+    return cudaGetLastError();
+}
 cudaError_t launch_default_refs(ld_ctx* c) { return default_refs(c); }
 int choose_step_kernel(int nx, int ny, int nz, int prec, int requested) {
     const bool f64p = prec == LD_FP64;
-    const bool tma = f64p ? f64::tma_supported(nx, ny, nz, prec) : lp::tma_supported(nx, ny, nz, prec);
+    const bool staged = f64p ? f64::staged_supported(nx, ny, nz, prec) : lp::staged_supported(nx, ny, nz, prec);
     const bool regs = f64p ? f64::regs_supported(nx, ny, nz) : lp::regs_supported(nx, ny, nz);
     switch (requested) {
         case LD_KERNEL_GENERIC: return kStepGeneric;
         case LD_KERNEL_FUSED: return regs ? kStepRegs : 0;
-        case LD_KERNEL_FUSED_TMA: return tma ? kStepTma : 0;
+        case LD_KERNEL_FUSED_STAGED: return staged ? kStepStaged : 0;
         // FP64 is bound by the FP64 pipe, and the three row-ordered launches
         // do less FP64 work per site than the fused step (no halo phi sums)
         case LD_KERNEL_AUTO: return regs && !f64p ? kStepRegs : kStepGeneric;

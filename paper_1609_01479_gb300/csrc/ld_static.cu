@@ -11,7 +11,9 @@
 //
 // The first call on each device looks up that array's device address with
 // cudaGetSymbolAddress (with the device current) and caches it; make that
-// first call before any stream capture. All calls share the array: calls
+// first call before any stream capture. The cached address belongs to the
+// device's primary context, so after cudaDeviceReset the call is invalid
+// for the rest of the process. All calls share the array: calls
 // that overlap on the GPU (on different streams without ordering between
 // them) race on it and their results are undefined. Each call writes every
 // partial it later reads, so nothing has to start at zero.

@@ -20,12 +20,12 @@ import torch
 from . import build as _build
 
 LD_FP64, LD_FP32, LD_FP16DEV, LD_BF16DEV = 0, 1, 2, 3
-LD_KERNEL_AUTO, LD_KERNEL_GENERIC, LD_KERNEL_FUSED, LD_KERNEL_FUSED_TMA = 0, 1, 2, 3
+LD_KERNEL_AUTO, LD_KERNEL_GENERIC, LD_KERNEL_FUSED, LD_KERNEL_FUSED_STAGED = 0, 1, 2, 3
 LD_OK, LD_EINVAL, LD_ECUDA, LD_ENONFINITE, LD_ESTATE = 0, -1, -2, -3, -4
 
 PRECISIONS = {"fp64": LD_FP64, "fp32": LD_FP32, "fp16dev": LD_FP16DEV, "bf16dev": LD_BF16DEV}
 KERNELS = {"auto": LD_KERNEL_AUTO, "generic": LD_KERNEL_GENERIC, "fused": LD_KERNEL_FUSED,
-           "fused_tma": LD_KERNEL_FUSED_TMA}
+           "fused_staged": LD_KERNEL_FUSED_STAGED}
 STORE_BYTES = {LD_FP64: 8, LD_FP32: 4, LD_FP16DEV: 2, LD_BF16DEV: 2}
 LD_STENCIL_7, LD_STENCIL_19 = 0, 1
 STENCILS = {7: LD_STENCIL_7, 19: LD_STENCIL_19}
@@ -65,9 +65,16 @@ _SIGNATURES = {
     "ld_set_stream": (ctypes.c_int, [_VP, _VP]),
     "ld_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(LdParams)]),
     "ld_init": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "ld_init_with_reference": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double]),
+    "ld_field_sum": (ctypes.c_int, [_VP, ctypes.c_longlong, _VP, _VP]),
+    "ld_planes_bytes": (ctypes.c_size_t, [_VP, ctypes.c_int]),
+    "ld_pack_planes": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP]),
+    "ld_unpack_planes": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP]),
     "ld_step": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "ld_step_kernel": (ctypes.c_int, [_VP]),
     "ld_moments": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "ld_check": (ctypes.c_int, [_VP]),
+    "ld_test_bounded_wait": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "ld_get_distributions": (ctypes.c_int, [_VP, _VP, _VP]),
     "ld_set_distributions": (ctypes.c_int, [_VP, _VP, _VP]),
     "ld_propagate": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -84,6 +91,7 @@ _SIGNATURES = {
     "ld_adjoint_get": (ctypes.c_int, [_VP, _VP, _VP]),
     "ld_adjoint_set": (ctypes.c_int, [_VP, _VP, _VP]),
     "ld_totals_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP]),
+    "ld_probe_fp64_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "ld_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ld_last_error": (ctypes.c_char_p, [_VP]),
 }
@@ -176,6 +184,35 @@ def ld_init(ctx, phi, rho=None, u=None):
     return _call("ld_init", ctx, _ptr(phi), _ptr(rho), _ptr(u))
 
 
+def ld_init_with_reference(ctx, phi, rho=None, u=None, phi_mean=0.0):
+    return _call("ld_init_with_reference", ctx, _ptr(phi), _ptr(rho), _ptr(u), float(phi_mean))
+
+
+def ld_field_sum(ctx, x, out):
+    return _call("ld_field_sum", ctx, ctypes.c_longlong(x.numel()), _ptr(x), _ptr(out))
+
+
+def ld_planes_bytes(ctx, nplanes: int) -> int:
+    return int(lib().ld_planes_bytes(ctx, int(nplanes)))
+
+
+def ld_pack_planes(ctx, z0: int, nplanes: int, buf):
+    return _call("ld_pack_planes", ctx, int(z0), int(nplanes), _ptr(buf))
+
+
+def ld_unpack_planes(ctx, z0: int, nplanes: int, buf):
+    return _call("ld_unpack_planes", ctx, int(z0), int(nplanes), _ptr(buf))
+
+
+def ld_step_kernel(ctx) -> str:
+    """Name of the step kernel the context runs (AUTO resolved)."""
+    code = lib().ld_step_kernel(ctx)
+    names = {v: k for k, v in KERNELS.items()}
+    if code not in names:
+        raise LdError(code, "ld_step_kernel", "invalid context")
+    return names[code]
+
+
 def ld_step(ctx, nsteps: int):
     return _call("ld_step", ctx, int(nsteps))
 
@@ -186,6 +223,10 @@ def ld_moments(ctx, rho=None, u=None, phi=None, grad_phi=None, totals=None):
 
 def ld_check(ctx):
     return _call("ld_check", ctx)
+
+
+def ld_test_bounded_wait(ctx, max_polls: int, probe: bool):
+    return _call("ld_test_bounded_wait", ctx, int(max_polls), int(bool(probe)))
 
 
 def ld_get_distributions(ctx, f=None, g=None):
@@ -249,11 +290,39 @@ def ld_adjoint_set(ctx, fbar, gbar):
 
 
 def ld_totals_static(nx, ny, nz, f, g, totals, stream=None):
-    """Allocation-free FP64 totals of double[19][N] distributions (see ld.h)."""
-    s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream(f.device).cuda_stream)
-    rc = lib().ld_totals_static(nx, ny, nz, _ptr(f), _ptr(g), _ptr(totals), s)
+    """Allocation-free FP64 totals of double[19][N] distributions (see ld.h).
+
+    The library can check only the size limit of its static scratch, not the
+    extent of the buffers it is given, so the tensors are checked here before
+    any launch: f and g float64 with at least 19 nx ny nz elements, totals
+    float64 with at least 5, all three on one CUDA device. The call runs with
+    that device current."""
+    n = int(nx) * int(ny) * int(nz)
+    for name, t, need in (("f", f, Q * n), ("g", g, Q * n), ("totals", totals, 5)):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"ld_totals_static: {name} must be a torch.Tensor")
+        if t.dtype != torch.float64:
+            raise ValueError(f"ld_totals_static: {name} must be float64, got {t.dtype}")
+        if t.numel() < need:
+            raise ValueError(f"ld_totals_static: {name} holds {t.numel()} values, {need} needed")
+    if not (f.device == g.device == totals.device):
+        raise ValueError("ld_totals_static: f, g and totals must be on one device")
+    with torch.cuda.device(f.device):
+        s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream(f.device).cuda_stream)
+        rc = lib().ld_totals_static(nx, ny, nz, _ptr(f), _ptr(g), _ptr(totals), s)
     if rc != LD_OK:
         raise LdError(rc, "ld_totals_static", lib().ld_last_error(None).decode(errors="replace"))
+    return rc
+
+
+def ld_probe_fp64_rate(op: int, blocks: int, iters: int, sink, stream=None):
+    """Launch the FP64 throughput probe (see ld.h); the caller times it."""
+    if sink.dtype != torch.float64 or sink.numel() < blocks:
+        raise ValueError("ld_probe_fp64_rate: sink must be float64 with at least `blocks` values")
+    s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream(sink.device).cuda_stream)
+    rc = lib().ld_probe_fp64_rate(int(op), int(blocks), int(iters), _ptr(sink), s)
+    if rc != LD_OK:
+        raise LdError(rc, "ld_probe_fp64_rate", lib().ld_last_error(None).decode(errors="replace"))
     return rc
 
 

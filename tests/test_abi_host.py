@@ -95,13 +95,13 @@ def test_workspace_bytes_validates_the_options(ld):
     ws = ld.ld_workspace_bytes
     base = ws(32, 8, 8, ld.make_params(precision="fp32"))
     assert base > 0
-    # 19-point stencils: not on the TMA-staged kernel
+    # 19-point stencils: every kernel
     assert ws(32, 8, 8, ld.make_params(precision="fp32", stencil=19)) == base
-    assert ws(32, 8, 8, ld.make_params(precision="fp32", stencil=19, kernel="fused_tma")) == 0
+    assert ws(32, 8, 8, ld.make_params(precision="fp32", stencil=19, kernel="fused_staged")) == base
     # the stress force: generic kernel only, six stress fields in the workspace
     stress = ws(32, 8, 8, ld.make_params(precision="fp32", force="stress"))
     assert stress >= base + 6 * 32 * 8 * 8 * 4
-    for kernel in ("fused", "fused_tma"):
+    for kernel in ("fused", "fused_staged"):
         assert ws(32, 8, 8, ld.make_params(precision="fp32", force="stress", kernel=kernel)) == 0
     assert ws(32, 8, 8, ld.make_params(precision="fp32", force=7)) == 0
     # TRT: generic kernel only, positive magic parameter
@@ -109,11 +109,31 @@ def test_workspace_bytes_validates_the_options(ld):
     assert ws(32, 8, 8, ld.make_params(precision="fp32", collision="trt", kernel="fused")) == 0
     assert ws(32, 8, 8, ld.make_params(precision="fp32", collision="trt", magic=0.0)) == 0
     assert ws(32, 8, 8, ld.make_params(precision="fp32", collision=3)) == 0
-    # stochastic rounding: the 16-bit forms only, not on the TMA-staged kernel
+    # stochastic rounding: the 16-bit forms only, on every kernel
     for prec in ("fp16dev", "bf16dev"):
         nearest = ws(32, 8, 8, ld.make_params(precision=prec))
         assert ws(32, 8, 8, ld.make_params(precision=prec, rounding="stochastic", seed=2**64 - 1)) == nearest
-        assert ws(32, 8, 8, ld.make_params(precision=prec, rounding="stochastic", kernel="fused_tma")) == 0
+        assert ws(32, 8, 8, ld.make_params(precision=prec, rounding="stochastic", kernel="fused_staged")) == nearest
     for prec in ("fp64", "fp32"):
         assert ws(32, 8, 8, ld.make_params(precision=prec, rounding="stochastic")) == 0
     assert ws(32, 8, 8, ld.make_params(precision="fp16dev", rounding=2)) == 0
+    assert ws(32, 8, 8, ld.make_params(precision="fp32", kernel=4)) == 0
+
+
+def test_static_totals_wrapper_checks_buffers_before_any_launch(ld):
+    """The library can check only the size limit of its static scratch, so
+    the binding refuses buffers of the wrong type or extent on the host,
+    before a pointer reaches the library (these CPU tensors never do)."""
+    import torch
+
+    n = 16 * 16 * 16
+    f = torch.zeros(19 * n, dtype=torch.float64)
+    out = torch.zeros(5, dtype=torch.float64)
+    with pytest.raises(ValueError, match="needed"):
+        ld.ld_totals_static(16, 16, 16, f[:-1], f, out)  # one value short, well under the size limit
+    with pytest.raises(ValueError, match="needed"):
+        ld.ld_totals_static(16, 16, 16, f, f, out[:4])
+    with pytest.raises(ValueError, match="float64"):
+        ld.ld_totals_static(16, 16, 16, f.float(), f, out)
+    with pytest.raises(TypeError):
+        ld.ld_totals_static(16, 16, 16, f.numpy(), f, out)

@@ -113,15 +113,33 @@ def test_gradient_by_central_differences_8cube(mods):
         assert g == pytest.approx(fdv, rel=1e-6)
 
 
+def oracle_tau_f_grad_fp32_storage(phi0, target, prm, steps):
+    """dL/dtau_f by the oracle's tangent-linear model along a trajectory whose
+    distributions are rounded to FP32 after the initialiser and after every
+    step (the tangent itself stays FP64): what FP32 storage alone does to
+    the exact derivative."""
+    rnd = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+    f, g = oracle.init(phi0, prm)
+    f, g = rnd(f), rnd(g)
+    df, dg = np.zeros_like(f), np.zeros_like(g)
+    dprm = np.zeros(7)
+    dprm[4] = 1.0
+    for _ in range(steps):
+        f, g, df, dg = oracle.step_tl(f, g, df, dg, prm, dprm, 1)
+        f, g = rnd(f), rnd(g)
+    return float(2.0 * ((g.sum(axis=0) - target) * dg.sum(axis=0)).sum())
+
+
 @pytest.mark.parametrize("kernel", ["fused", "generic"])
 def test_dot_product_fp32(mods, kernel):
     """FP32 storage and FP32 adjoint arithmetic against the FP64 oracle:
     dL/dphi0 (along a random direction) and dL/dkappa within 1e-4.
-    dL/dtau_f acts on phi only through the flow u = (j + F/2)/rho, and j is a
-    cancellation of O(w_i) values: FP32 storage of f leaves u a relative
-    rounding error of order 2^-24 * sum|f_i| / |j| ~ 1e-3 at |u| ~ 1e-4, so
-    dL/dtau_f is held to 1e-3. The residual phi_T - target (kappa_target =
-    0.08) stays far above the FP32 error of phi_T."""
+
+    dL/dtau_f is held to 1e-3 (measured errors are printed). The oracle's
+    exact tangent-linear model run along a trajectory rounded to FP32 after
+    every step is reported beside it: the share of that error FP32 storage
+    alone would cause. The residual phi_T - target (kappa_target = 0.08)
+    stays far above the FP32 error of phi_T."""
     ld, adjoint = mods
     nz, ny, nx = 16, 16, 32
     steps = 60
@@ -133,14 +151,18 @@ def test_dot_product_fp32(mods, kernel):
     rng = np.random.default_rng(8)
     dphi = rng.standard_normal(phi0.shape)
     _, dL = oracle.loss_jvp(phi0, target, prm, steps, dphi0=dphi)
-    assert float((gphi * dphi).sum()) == pytest.approx(dL, rel=1e-4)
-    errs = {}
+    errs = {"dphi0": abs(float((gphi * dphi).sum()) - dL) / abs(dL)}
+    exact = {}
     for name, idx, g in (("kappa", 2, gk), ("tau_f", 4, gt)):
         dprm = np.zeros(7)
         dprm[idx] = 1.0
-        _, dL = oracle.loss_jvp(phi0, target, prm, steps, dprm=dprm)
-        errs[name] = abs(g - dL) / abs(dL)
-    assert errs["kappa"] <= 1e-4 and errs["tau_f"] <= 1e-3, errs
+        _, exact[name] = oracle.loss_jvp(phi0, target, prm, steps, dprm=dprm)
+        errs[name] = abs(g - exact[name]) / abs(exact[name])
+    storage = oracle_tau_f_grad_fp32_storage(phi0, target, prm, steps)
+    errs["tau_f_storage_only"] = abs(storage - exact["tau_f"]) / abs(exact["tau_f"])
+    print(f"\n[adjoint fp32 {kernel}] relative errors: {errs}")
+    assert errs["dphi0"] <= 1e-4 and errs["kappa"] <= 1e-4, errs
+    assert errs["tau_f"] <= 1e-3, errs
 
 
 def test_zero_loss_gives_zero_gradient(mods):

@@ -12,6 +12,7 @@ import pytest
 import torch
 
 import oracle
+from oracle_floors import oracle_u_floor
 from paper_1609_01479_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -65,21 +66,6 @@ def oracle_run(phi, steps, prm=None, rho=None, u=None):
     m = oracle.macros(f, g, prm)
     m["f"], m["g"] = f, g
     return m
-
-
-def oracle_u_floor(phi, steps, prm=None, rho=None, u=None):
-    """Relative L2 change of the oracle's own u after `steps` steps when its
-    initial distributions move by at most one ulp: the rounding floor of u.
-    u = (j + F/2)/rho is a cancellation of O(w_i) values, so when |u| is small
-    this floor can exceed 1e-12 (7.7e-12 for the 16^3 spinodal at 100 steps)."""
-    prm = oracle.param_vector() if prm is None else prm
-    f, g = oracle.init(phi, prm, rho=rho, u=u)
-    rng = np.random.default_rng(1234)
-    fp = f + np.spacing(f) * rng.choice([-1.0, 0.0, 1.0], size=f.shape)
-    gp = g + np.spacing(g) * rng.choice([-1.0, 0.0, 1.0], size=g.shape)
-    a = oracle.macros(*oracle.step(f, g, prm, steps), prm)["u"]
-    b = oracle.macros(*oracle.step(fp, gp, prm, steps), prm)["u"]
-    return rel_l2(b, a)
 
 
 def assert_parity(gpu, ref, tol, fields=("rho", "u", "phi", "grad_phi", "f", "g"), u_tol=None):
@@ -188,7 +174,7 @@ def test_reduced_precision_stress_force(ld, precision, tol):
 
 def test_stress_force_refusals(ld):
     """The stress form runs on the generic launches and has no adjoint."""
-    for kernel in ("fused", "fused_tma"):
+    for kernel in ("fused", "fused_staged"):
         with pytest.raises(ld.LdError) as e:
             ld.LdSim(32, 8, 4, precision="fp32", kernel=kernel, force="stress")
         assert e.value.code == ld.LD_EINVAL
@@ -230,7 +216,7 @@ def test_reduced_precision_trt(ld, precision, tol):
 
 
 def test_trt_refusals(ld):
-    for kernel in ("fused", "fused_tma"):
+    for kernel in ("fused", "fused_staged"):
         with pytest.raises(ld.LdError) as e:
             ld.LdSim(32, 8, 4, precision="fp32", kernel=kernel, collision="trt")
         assert e.value.code == ld.LD_EINVAL
@@ -243,10 +229,21 @@ def test_trt_refusals(ld):
     sim.close()
 
 
-def test_isotropic_stencils_refused_by_the_tma_kernel(ld):
-    with pytest.raises(ld.LdError) as e:
-        ld.LdSim(32, 8, 4, precision="fp32", kernel="fused_tma", stencil=19)
-    assert e.value.code == ld.LD_EINVAL
+@pytest.mark.parametrize("precision", ["fp32", "fp16dev"])
+@pytest.mark.parametrize("stencil", [7, 19])
+def test_staged_and_register_fused_kernels_agree(ld, precision, stencil):
+    """The staged kernel runs the register kernel's arithmetic on the same
+    values (it changes only how they reach the threads), so the two agree
+    far inside the storage bound, with either stencil pair."""
+    nz, ny, nx = 12, 24, 96
+    phi = inputs.spinodal_phi(nx, ny, nz, seed=19, amplitude=0.3)
+    prm = oracle.param_vector(stencil=stencil)
+    a = gpu_run(ld, phi, 15, precision=precision, kernel="fused", prm=prm)
+    b = gpu_run(ld, phi, 15, precision=precision, kernel="fused_staged", prm=prm)
+    same = {"fp32": 1e-6, "fp16dev": 2e-3}[precision]
+    assert rel_l2(b["phi"], a["phi"]) <= same
+    assert rel_l2(b["f"], a["f"]) <= same
+    assert rel_l2(b["g"], a["g"]) <= same
 
 
 def test_fp64_fused_with_flow_and_density(ld):
@@ -359,7 +356,7 @@ def test_save_load_roundtrip(ld):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16dev", 1e-2), ("bf16dev", 1e-1)])
-@pytest.mark.parametrize("kernel", ["generic", "fused", "fused_tma"])
+@pytest.mark.parametrize("kernel", ["generic", "fused", "fused_staged"])
 def test_reduced_precision_error(ld, precision, tol, kernel):
     nz, ny, nx = 32, 32, 32
     phi = inputs.spinodal_phi(nx, ny, nz, seed=2)
@@ -373,17 +370,17 @@ def test_reduced_precision_error(ld, precision, tol, kernel):
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
 @pytest.mark.parametrize("shape", [(4, 8, 32), (8, 16, 64), (12, 24, 96), (16, 48, 32)])
-def test_tma_kernel_matches_oracle_and_generic(ld, precision, shape):
-    """The TMA-staged fused kernel on lattices that exercise every periodic
-    edge of its copies: one tile across x (nx = 32) or y, edge tiles on both
-    sides, z-chunks whose halo planes wrap (nz = 4, 12). Same arithmetic as the
+def test_staged_kernel_matches_oracle_and_generic(ld, precision, shape):
+    """The staged fused kernel on lattices that exercise every periodic edge
+    of its copies: one tile across x (nx = 32) or y, edge tiles on both sides,
+    z-chunks whose halo planes wrap (nz = 4, 12). Same arithmetic as the
     generic kernel up to FMA contraction; against the FP64 oracle within the
     storage-precision bound."""
     nz, ny, nx = shape
     phi = inputs.spinodal_phi(nx, ny, nz, seed=13, amplitude=0.3)
     steps = 15
     a = gpu_run(ld, phi, steps, precision=precision, kernel="generic")
-    b = gpu_run(ld, phi, steps, precision=precision, kernel="fused_tma")
+    b = gpu_run(ld, phi, steps, precision=precision, kernel="fused_staged")
     r = oracle_run(phi, steps)
     tol = {"fp32": 1e-5, "fp16dev": 1e-2, "bf16dev": 1e-1}[precision]
     assert rel_l2(b["phi"], r["phi"]) <= tol
@@ -400,7 +397,7 @@ def test_generic_and_fused_agree(ld):
     nz, ny, nx = 8, 16, 64
     phi = inputs.spinodal_phi(nx, ny, nz, seed=12, amplitude=0.4)
     a = gpu_run(ld, phi, 30, precision="fp32", kernel="generic")
-    for kernel in ("fused", "fused_tma"):
+    for kernel in ("fused", "fused_staged"):
         b = gpu_run(ld, phi, 30, precision="fp32", kernel=kernel)
         assert rel_l2(b["phi"], a["phi"]) < 1e-6
         assert rel_l2(b["f"], a["f"]) < 1e-6

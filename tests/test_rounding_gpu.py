@@ -73,7 +73,7 @@ def _check_decisions(stored, exact, ref, keys, fmt):
 
 
 @pytest.mark.parametrize("precision", ["fp16dev", "bf16dev"])
-@pytest.mark.parametrize("kernel", ["fused", "generic"])
+@pytest.mark.parametrize("kernel", ["fused", "fused_staged", "generic"])
 @pytest.mark.parametrize("t", [0, 3])
 def test_stochastic_stores_match_the_checker(ld, precision, kernel, t):
     """One step at step counter t from a known state: every store the FP32
@@ -151,15 +151,12 @@ def test_stochastic_runs_are_reproducible_and_seeded(ld):
 
 
 def test_stochastic_rounding_refusals(ld):
-    """Stochastic rounding is for the 16-bit forms, not the TMA-staged
-    kernel, not ld_step_between or the adjoint, and fixed at creation."""
+    """Stochastic rounding is for the 16-bit forms, not ld_step_between or
+    the adjoint, and fixed at creation."""
     for precision in ("fp64", "fp32"):
         with pytest.raises(ld.LdError) as e:
             ld.LdSim(32, 8, 4, precision=precision, rounding="stochastic")
         assert e.value.code == ld.LD_EINVAL
-    with pytest.raises(ld.LdError) as e:
-        ld.LdSim(32, 8, 4, precision="fp16dev", kernel="fused_tma", rounding="stochastic")
-    assert e.value.code == ld.LD_EINVAL
     sim = ld.LdSim(32, 8, 4, precision="bf16dev", rounding="stochastic", seed=1)
     sim.init(torch.zeros(4, 8, 32, dtype=torch.float64, device="cuda"))
     assert ld.ld_adjoint_workspace_bytes(sim.ctx) == 0
