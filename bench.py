@@ -102,7 +102,8 @@ def _code_hash(rels):
 
 
 def kernel_source_hash():
-    return _code_hash(("paper_1609_01479_gb300/csrc/ld_fused.cuh", "paper_1609_01479_gb300/csrc/ld_common.cuh"))
+    return _code_hash(("paper_1609_01479_gb300/csrc/ld_fused.cuh", "paper_1609_01479_gb300/csrc/ld_common.cuh",
+                       "paper_1609_01479_gb300/csrc/ld_async.cuh"))
 
 
 def fp64_source_hash():

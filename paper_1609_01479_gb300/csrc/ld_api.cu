@@ -392,6 +392,7 @@ int ld_check(ld_ctx* c) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ld_check");
+    if (status & ld::kStatusBounds) return fail(c, LD_ECUDA, "a kernel caught a site index outside the lattice (debug build, status %d)", status);
     if (status) return fail(c, LD_ECUDA, "a kernel gave up waiting for its shared-memory copies (status %d)", status);
     for (int k = 0; k < 5; ++k)
         if (!isfinite(host[k])) return fail(c, LD_ENONFINITE, "state holds a non-finite value (total %d)", k);

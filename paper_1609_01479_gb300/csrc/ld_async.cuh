@@ -9,10 +9,9 @@
 #include <stdint.h>
 #include <string.h>
 
-namespace ld {
+#include "ld_common.cuh"
 
-// Status bits written by kernels into the workspace status word.
-constexpr int kStatusWaitTimeout = 1;
+namespace ld {
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -111,14 +110,9 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint64
                  : "memory");
 }
 
-// Arrive once on the barrier when all of this thread's earlier cp.async
-// copies have landed, without raising the phase's expected count (the
-// barrier is initialised with the number of threads that arrive this way).
-__device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// Block until every cp.async copy this thread issued has landed.
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Close the group of this thread's cp.async copies issued so far; wait until
+// all of its groups have landed (a hardware wait: the copies always land).
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_group0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 }  // namespace ld

@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "ld.h"
+#include "ld_internal.h"
 
 namespace ld {
 
@@ -137,6 +138,23 @@ __device__ __forceinline__ unsigned sr_key(const SrStream& r, unsigned long long
                                            unsigned long long& w) {
     if ((i & 3) == 0) w = sr_mix(st + (unsigned long long)(5 * a + (i >> 2)) * r.stride);
     return (unsigned)(w >> (16 * (i & 3))) & 0xffffu;
+}
+
+// Debug builds (compiled with -DLD_DEBUG_BOUNDS): the step kernels check the
+// site index of every global load and store against [0, n) first; an index
+// outside sets kStatusBounds and the access is skipped (a load reads 0), so
+// a wrong index is reported instead of faulting. Release builds compile the
+// checks away.
+#ifdef LD_DEBUG_BOUNDS
+constexpr bool kDebugBounds = true;
+#else
+constexpr bool kDebugBounds = false;
+#endif
+__device__ __forceinline__ bool site_ok(long long s, long long n, int* status) {
+    if constexpr (!kDebugBounds) return true;
+    if (s >= 0 && s < n) return true;
+    atomicOr(status, kStatusBounds);
+    return false;
 }
 
 // Lattice geometry. npad: component stride of every SoA array (>= n, a

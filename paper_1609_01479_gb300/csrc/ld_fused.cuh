@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
                  const typename Prec<P>::store_t* __restrict__ fs, const typename Prec<P>::store_t* __restrict__ gs,
                  typename Prec<P>::store_t* __restrict__ fd, typename Prec<P>::store_t* __restrict__ gd,
                  const float* __restrict__ ref_g, typename Prec<P>::real_t* __restrict__ phi_out,
-                 typename Prec<P>::real_t* __restrict__ mu_out, SrStream sr) {
+                 typename Prec<P>::real_t* __restrict__ mu_out, SrStream sr, int* __restrict__ status) {
     using R = typename Prec<P>::real_t;
     using S = typename Prec<P>::store_t;
     constexpr int PW = kTX + 4, PH = TY + 4;  // phi ring plane
@@ -108,17 +108,18 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
                 const int hx = 2 * (idx % PW2), hy = idx / PW2;
                 const int gx = wrap_once(x0 + hx - 2, nx), gy = wrap_once(y0 + hy - 2, ny);
                 const int s = zoff + gy * nx + gx;  // even
+                const bool sok = site_ok(s, g.n, status) && site_ok(s + 1, g.n, status);
                 const bool interior = kKeepG && hx >= 2 && hx < kTX + 2 && hy >= 2 && hy < TY + 2;
                 S* keep = gring + ((size_t)slot * Q * TY + (hy - 2)) * kTX + (hx - 2);
                 R a0 = R(0), a1 = R(0);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     if constexpr (sizeof(S) == 4) {
-                        const float2 v = ld_l2_hint_pair(gs + i * npad + s, keep_l2);
+                        const float2 v = sok ? ld_l2_hint_pair(gs + i * npad + s, keep_l2) : make_float2(0.f, 0.f);
                         a0 += v.x;
                         a1 += v.y;
                     } else {  // psi: the sum of the deviations
-                        const unsigned v = ld_l2_hint_pair(gs + i * npad + s, keep_l2);
+                        const unsigned v = sok ? ld_l2_hint_pair(gs + i * npad + s, keep_l2) : 0u;
                         if constexpr (P == LD_FP16DEV) {
                             a0 = add_f16(a0, (unsigned short)(v & 0xffffu));
                             a1 = add_f16(a1, (unsigned short)(v >> 16));
@@ -137,12 +138,13 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
                 const int hx = idx % PW, hy = idx / PW;
                 const int gx = wrap_once(x0 + hx - 2, nx), gy = wrap_once(y0 + hy - 2, ny);
                 const int s = zoff + gy * nx + gx;
+                const bool sok = site_ok(s, g.n, status);
                 const bool interior = kKeepG && hx >= 2 && hx < kTX + 2 && hy >= 2 && hy < TY + 2;
                 S* keep = gring + ((size_t)slot * Q * TY + (hy - 2)) * kTX + (hx - 2);
                 R acc = R(0);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
-                    const S v = ld_l2_hint(gs + i * npad + s, keep_l2);
+                    const S v = sok ? ld_l2_hint(gs + i * npad + s, keep_l2) : S(0);
                     acc += Prec<P>::decode(v, refs[Q + i]);
                     if (interior) keep[i * (TY * kTX)] = v;
                 }
@@ -194,6 +196,7 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     for (int k = z0; k < z0 + zc; ++k) {
         const int z = k;  // zc divides nz: k < nz
         const int s = z * plane + y * nx + x;
+        const bool cok = site_ok(s, g.n, status);
         // Loads for this plane's collision issued ahead of the phi and mu
         // passes, so that their latency overlaps that work: in FP32 the g
         // re-read (an L2 hit), in the 16-bit forms (g kept in shared memory)
@@ -202,13 +205,13 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
         S gpre[Q], fpre[Q];
         if constexpr (kEarlyG) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) gpre[i] = ld_l2_hint_now(gs + i * npad + s, drop_l2);
+            for (int i = 0; i < Q; ++i) gpre[i] = cok ? ld_l2_hint_now(gs + i * npad + s, drop_l2) : S(0);
         }
         __syncthreads();  // previous collision done with phi(k-1) and mu(k-2) slots
         phi_plane(k + 2, ps(k + 2));
         if constexpr (kKeepG) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) fpre[i] = ld_l2_hint_now(fs + i * npad + s, drop_l2);
+            for (int i = 0; i < Q; ++i) fpre[i] = cok ? ld_l2_hint_now(fs + i * npad + s, drop_l2) : S(0);
         }
         __syncthreads();
         mu_plane(ms(k + 1), ps(k), ps(k + 1), ps(k + 2));
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
             gmz = R(0.5) * (mus[ms(k + 1)][ty + 1][tx + 1] - mus[ms(k - 1)][ty + 1][tx + 1]);
         }
         const R Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
-        if (phi_out) {  // fields of the source state, for the adjoint
+        if (phi_out && cok) {  // fields of the source state, for the adjoint
             phi_out[s] = ph;
             mu_out[s] = muc;
         }
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
             R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                f[i] = Prec<P>::decode(fs[i * npad + s], refs[i]);
+                f[i] = Prec<P>::decode(cok ? fs[i * npad + s] : S(0), refs[i]);
                 rho += f[i];
                 add_c(i, f[i], jx, jy, jz);
             }
@@ -272,10 +275,13 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const R ref = kKeepG ? R(0) : refs[i];  // deviations are stored as they are
+            const int d = dest(i);
+            S v;
             if constexpr (SR)
-                __stcs(fd + i * npad + dest(i), Prec<P>::encode_sr(f[i], ref, sr_key(sr, sr_st, 0, i, sr_w)));
+                v = Prec<P>::encode_sr(f[i], ref, sr_key(sr, sr_st, 0, i, sr_w));
             else
-                __stcs(fd + i * npad + dest(i), Prec<P>::encode(f[i], ref));
+                v = Prec<P>::encode(f[i], ref);
+            if (site_ok(d, g.n, status)) __stcs(fd + i * npad + d, v);
         }
 
         R gg[Q];
@@ -286,7 +292,7 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
         } else {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const S v = kEarlyG ? gpre[i] : ld_l2_hint(gs + i * npad + s, drop_l2);
+                const S v = kEarlyG ? gpre[i] : (cok ? ld_l2_hint(gs + i * npad + s, drop_l2) : S(0));
                 gg[i] = Prec<P>::decode(v, refs[Q + i]);
             }
             collide_g(gg, ph, muc, ux, uy, uz, m);
@@ -294,10 +300,13 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const R ref = kKeepG ? R(0) : refs[Q + i];
+            const int d = dest(i);
+            S v;
             if constexpr (SR)
-                __stcs(gd + i * npad + dest(i), Prec<P>::encode_sr(gg[i], ref, sr_key(sr, sr_st, 1, i, sr_w)));
+                v = Prec<P>::encode_sr(gg[i], ref, sr_key(sr, sr_st, 1, i, sr_w));
             else
-                __stcs(gd + i * npad + dest(i), Prec<P>::encode(gg[i], ref));
+                v = Prec<P>::encode(gg[i], ref);
+            if (site_ok(d, g.n, status)) __stcs(gd + i * npad + d, v);
         }
     }
 }
@@ -338,7 +347,7 @@ cudaError_t launch_fused(ld_ctx* c, const void* src, void* dst, void* fields) {
     k_step_fused<P, kTY, I, ISO, SR><<<grid, kTX * kTY, kRingBytes, c->stream>>>(
         g, model_of<R>(c->prm), zc, (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
         (S*)g_part(c, dst), c->ref, fields ? (R*)fields : nullptr, fields ? (R*)fields + c->geom.npad : nullptr,
-        sr_stream(c->prm.seed, c->sr_step, c->geom.n));
+        sr_stream(c->prm.seed, c->sr_step, c->geom.n), c->status);
     return cudaGetLastError();
 }
 

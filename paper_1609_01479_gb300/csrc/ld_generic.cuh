@@ -65,10 +65,11 @@ __device__ __forceinline__ bool row_site(const RowGeom& rg, int b, int& x, int& 
 template <int P, class I>
 __global__ void __launch_bounds__(kRowThreads) k_phi(RowGeom rg, I npad, const typename Prec<P>::store_t* __restrict__ gs,
                                                      const float* __restrict__ ref,
-                                                     typename Prec<P>::real_t* __restrict__ phi) {
+                                                     typename Prec<P>::real_t* __restrict__ phi, int* __restrict__ status) {
     using R = typename Prec<P>::real_t;
     int x, y, z, s;
     if (!row_site(rg, blockIdx.x, x, y, z, s)) return;
+    if (!site_ok(s, (long long)rg.nx * rg.ny * rg.nz, status)) return;
     R acc = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) acc += Prec<P>::decode(gs[i * npad + s], ref[Q + i]);
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(kRowThreads, rows_blocks_per_sm<P>())
               const typename Prec<P>::store_t* __restrict__ gs, typename Prec<P>::store_t* __restrict__ fd,
               typename Prec<P>::store_t* __restrict__ gd, const typename Prec<P>::real_t* __restrict__ phi,
               const typename Prec<P>::real_t* __restrict__ mu, const float* __restrict__ ref,
-              const typename Prec<P>::real_t* __restrict__ stress) {
+              const typename Prec<P>::real_t* __restrict__ stress, int* __restrict__ status) {
     using R = typename Prec<P>::real_t;
     using S = typename Prec<P>::store_t;
     __shared__ float refs[2 * Q];  // codec references, read once per block
@@ -197,6 +198,8 @@ __global__ void __launch_bounds__(kRowThreads, rows_blocks_per_sm<P>())
     __syncthreads();
     int x, y, z, s;
     if (!row_site(rg, blockIdx.x, x, y, z, s)) return;
+    const long long n = (long long)rg.nx * rg.ny * rg.nz;
+    if (!site_ok(s, n, status)) return;
     // FP32 and FP64 issue all 38 loads first; the 16-bit forms issue g after
     // the f stores (each 16-bit value held early would take a register).
     constexpr bool kEarlyG = sizeof(S) >= 4;
@@ -242,10 +245,12 @@ __global__ void __launch_bounds__(kRowThreads, rows_blocks_per_sm<P>())
     for (int i = 0; i < Q; ++i) {
         const int d = s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
                       (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
+        S v;
         if constexpr (SR)
-            __stcs(fd + i * npad + d, Prec<P>::encode_sr(f[i], refs[i], sr_key(sr, sr_st, 0, i, sr_w)));
+            v = Prec<P>::encode_sr(f[i], refs[i], sr_key(sr, sr_st, 0, i, sr_w));
         else
-            __stcs(fd + i * npad + d, Prec<P>::encode(f[i], refs[i]));
+            v = Prec<P>::encode(f[i], refs[i]);
+        if (site_ok(d, n, status)) __stcs(fd + i * npad + d, v);
     }
     R gg[Q];
 #pragma unroll
@@ -255,10 +260,12 @@ __global__ void __launch_bounds__(kRowThreads, rows_blocks_per_sm<P>())
     for (int i = 0; i < Q; ++i) {
         const int d = s + (cx(i) > 0 ? oxp : (cx(i) < 0 ? oxm : 0)) + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) +
                       (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
+        S v;
         if constexpr (SR)
-            __stcs(gd + i * npad + d, Prec<P>::encode_sr(gg[i], refs[Q + i], sr_key(sr, sr_st, 1, i, sr_w)));
+            v = Prec<P>::encode_sr(gg[i], refs[Q + i], sr_key(sr, sr_st, 1, i, sr_w));
         else
-            __stcs(gd + i * npad + d, Prec<P>::encode(gg[i], refs[Q + i]));
+            v = Prec<P>::encode(gg[i], refs[Q + i]);
+        if (site_ok(d, n, status)) __stcs(gd + i * npad + d, v);
     }
 }
 
@@ -545,7 +552,8 @@ cudaError_t phi_mu_rows(ld_ctx* c, const void* state, void* fields) {
     const unsigned nb = row_blocks(c->geom);
     R* phi = fields ? (R*)fields : (R*)c->phi;
     R* mu = fields ? (R*)fields + c->geom.npad : (R*)c->mu;
-    k_phi<P, I><<<nb, kRowThreads, 0, c->stream>>>(rg, (I)c->geom.npad, (const S*)g_part(c, state), c->ref, phi);
+    k_phi<P, I><<<nb, kRowThreads, 0, c->stream>>>(rg, (I)c->geom.npad, (const S*)g_part(c, state), c->ref, phi,
+                                                   c->status);
     k_mu<R><<<nb, kRowThreads, 0, c->stream>>>(rg, model_of<R>(c->prm), phi, mu);
     return cudaGetLastError();
 }
@@ -571,7 +579,7 @@ cudaError_t collide_rows(ld_ctx* c, const void* src, void* dst, void* fields) {
     k_collide<P, I, SR><<<row_blocks(c->geom), kRowThreads, 0, c->stream>>>(
         row_geom(c->geom), (I)c->geom.npad, model_of<R>(c->prm), sr_stream(c->prm.seed, c->sr_step, c->geom.n),
         (const S*)f_part(c, src), (const S*)g_part(c, src),
-        (S*)f_part(c, dst), (S*)g_part(c, dst), phi, mu, c->ref, (const R*)c->stress);
+        (S*)f_part(c, dst), (S*)g_part(c, dst), phi, mu, c->ref, (const R*)c->stress, c->status);
     return cudaGetLastError();
 }
 

@@ -29,6 +29,11 @@ constexpr int kRedBlocks = 1024;
 constexpr int kRedThreads = 256;
 constexpr int kRedFields = 8;  // partial slots per block
 
+// Status bits written by kernels into the workspace status word (read by
+// ld_check).
+constexpr int kStatusWaitTimeout = 1;  // a bounded wait gave up
+constexpr int kStatusBounds = 2;       // debug builds: a site index fell outside the lattice
+
 // Poll limit of a kernel's barrier waits (mbarrier try_wait polls). Each
 // poll returns after at most a short hardware-defined suspension, so this
 // bounds a wait to well under a few seconds.

@@ -1,39 +1,28 @@
-// Fused single-pass step with asynchronously staged planes (FP32 and the
-// 16-bit storage forms).
+// Fused single-pass step with the f tile staged asynchronously (FP32 and
+// the 16-bit storage forms).
 //
-// Same decomposition and arithmetic as k_step_fused (ld_fused.cuh): a CTA of
-// 256 threads owns a 32 x 8 column of sites, marches up a chunk of z-planes
-// and keeps rolling phi and mu rings in shared memory. What differs is how
-// the distributions reach the threads. 16-byte cp.async copies, issued by
-// every thread and tracked on an mbarrier (cp.async.mbarrier.arrive.noinc),
-// stage one plane ahead of use:
-//   * the g box of plane k+3: 19 components x 12 rows (tile + 2-row halo in
-//     y) x (32 + 2 CH) values (tile + one 16-byte chunk of halo each side in
-//     x), issued once phi(k+2) is done with the box, so its latency overlaps
-//     mu(k+1) and the collision of plane k. Chunks wrap periodically on
-//     their own: nx is a multiple of 32, so a chunk never straddles the seam;
-//   * the f tile of plane k: 19 x 8 rows x 32 values, issued at the top of
-//     iteration k, so its latency overlaps the phi and mu passes.
-// The phi pass then sums g from shared memory. The collision's g is read
-// again with plain loads in FP32 (an L2 hit: the box copy brought those
-// lines in two planes earlier under an evict-last policy); the 16-bit forms
-// keep the tile's g of the last three planes in a shared-memory ring, filled
-// by the phi pass.
-// The 16-bit forms compute in deviation space (collide_f_dev and
-// collide_g_dev in ld_common.cuh): the phi ring holds psi = sum_i h_i (phi =
-// Phi + psi), each stored value enters its sum with one mixed-precision add,
-// and the collisions read and write deviations without adding or removing
-// the references.
+// Same decomposition, passes and arithmetic as k_step_fused (ld_fused.cuh):
+// a CTA of 256 threads owns a 32 x 8 column of sites, marches up a chunk of
+// z-planes, computes phi(k+2) over the tile + 2-halo from global loads into
+// a rolling ring, mu(k+1), then collides plane k and pushes it. What differs
+// is how the collision gets its f: every thread issues 16-byte cp.async
+// copies of the tile's f of plane k at the top of iteration k (19 x 8 rows x
+// 32 values into shared memory; each thread owns fixed 16-byte slots, so a
+// plane costs one address add per component), and waits for its own copies
+// (cp.async.wait_group, a hardware wait that ends when they land) before
+// the barrier that precedes the collision. Their latency overlaps the phi
+// and mu passes without holding registers. FP32 re-reads g with early
+// register loads and the 16-bit forms keep the tile's g in a ring, as in
+// k_step_fused; the 16-bit forms compute in deviation space.
+// Measured against k_step_fused it is slower (FP32 0.69 against 0.74 of the
+// measured HBM roofline at 384^3): the staged tile takes shared memory from
+// L1, where the collision's second read of g partly hits.
 //
-// Every wait is bounded (max_polls try_wait polls). A wait that gives up sets
-// kStatusWaitTimeout in the status word; the thread then stops waiting, lets
-// its own copies land (cp.async.wait_all) and finishes its loop on whatever
-// the staged buffers hold, so every thread still meets the same barriers and
-// the kernel returns; the step's result is then invalid, which ld_check
-// reports. `probe_wait` != 0 (a test setting, ld_test_bounded_wait) makes
-// every thread also wait, once, on a third barrier that nothing arrives on:
-// that wait runs out after max_polls polls with no copy tracked by it, sets
-// the status bit, and the step itself completes normally.
+// The kernel has one spin-wait, bounded: with `probe_wait` != 0 (a test
+// setting, ld_test_bounded_wait) every thread also waits, once, on an
+// mbarrier that nothing arrives on and that tracks no copy; that wait gives
+// up after max_polls polls, sets kStatusWaitTimeout in the status word
+// (ld_check reports it) and the step completes normally.
 // Template only: instantiated for FP32, FP16-dev and BF16-dev by ld_prec_lp.cu.
 #pragma once
 #include "ld_async.cuh"
@@ -49,23 +38,18 @@ struct StagedLayout {
     using S = typename Prec<P>::store_t;
     using R = typename Prec<P>::real_t;
     static constexpr int TX = 32, TY = 8, NT = TX * TY;
-    static constexpr int CH = 16 / (int)sizeof(S);   // values per 16-byte chunk
-    static constexpr int BW = TX + 2 * CH, BH = TY + 4;  // g box row width, rows
-    static constexpr int BCH = BW / CH;              // chunks per box row
-    static constexpr int FCH = TX / CH;              // chunks per f tile row
-    static constexpr int BOX_CHUNKS = Q * BH * BCH;
-    static constexpr int F_CHUNKS = Q * TY * FCH;
-    static constexpr bool kKeepG = sizeof(S) == 2;   // g ring of the last three planes (16-bit forms)
-    static constexpr size_t OFF_BOX = 0;
-    static constexpr size_t OFF_F = OFF_BOX + (size_t)Q * BH * BW * sizeof(S);
+    static constexpr int CH = 16 / (int)sizeof(S);  // values per 16-byte chunk
+    static constexpr int FCH = TX / CH;             // chunks per f tile row
+    static constexpr bool kDev = sizeof(S) == 2;    // deviation-space arithmetic and g ring (16-bit forms)
+    static constexpr size_t OFF_F = 0;
     static constexpr size_t OFF_RING = OFF_F + (size_t)Q * TY * TX * sizeof(S);
-    static constexpr size_t OFF_BAR = OFF_RING + (kKeepG ? 3 * (size_t)Q * TY * TX * sizeof(S) : 0);
-    static constexpr size_t BYTES = OFF_BAR + 3 * sizeof(unsigned long long);
-    // static shared memory: phi and mu rings, codec references
-    static constexpr size_t STATIC_BYTES =
-        3 * (size_t)(TY + 4) * (TX + 4) * sizeof(R) + 3 * (size_t)(TY + 2) * (TX + 2) * sizeof(R) + 2 * Q * 4;
+    static constexpr size_t OFF_BAR = OFF_RING + (kDev ? 3 * (size_t)Q * TY * TX * sizeof(S) : 0);
+    static constexpr size_t BYTES = OFF_BAR + sizeof(unsigned long long);
+    // static shared memory: phi and mu rings, codec references, deviation constants
+    static constexpr size_t STATIC_BYTES = 3 * (size_t)(TY + 4) * (TX + 4) * sizeof(R) +
+                                           3 * (size_t)(TY + 2) * (TX + 2) * sizeof(R) + 2 * Q * 4 + 64;
     static_assert(sizeof(S) == 4 || sizeof(S) == 2, "FP32 and 16-bit storage");
-    static_assert(OFF_F % 16 == 0 && OFF_RING % 16 == 0 && OFF_BAR % 8 == 0, "aligned regions");
+    static_assert(OFF_RING % 16 == 0 && OFF_BAR % 8 == 0, "aligned regions");
     // three CTAs per SM, each with 1 KB reserved by the hardware, in 228 KB
     static_assert(3 * (BYTES + STATIC_BYTES + 1024) <= 228 * 1024, "three CTAs per SM");
 };
@@ -80,21 +64,18 @@ __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
     using L = StagedLayout<P>;
     using R = typename L::R;
     using S = typename L::S;
-    constexpr int TX = L::TX, TY = L::TY, NT = L::NT, CH = L::CH, BW = L::BW, BH = L::BH;
+    constexpr int TX = L::TX, TY = L::TY, NT = L::NT, CH = L::CH;
     constexpr int PW = TX + 4, PH = TY + 4;  // phi ring plane
     constexpr int MW = TX + 2, MH = TY + 2;  // mu ring plane
-    constexpr bool kKeepG = L::kKeepG;
-    constexpr bool kEarlyG = !kKeepG;
+    constexpr bool kDev = L::kDev;
     __shared__ R phis[3][PH][PW];
     __shared__ R mus[3][MH][MW];
     __shared__ float refs[2 * Q];
     __shared__ DevRefs dref;  // deviation-space constants (16-bit forms)
     extern __shared__ __align__(128) unsigned char smem[];
-    S* box = reinterpret_cast<S*>(smem + L::OFF_BOX);    // [Q][BH][BW], x from x0 - CH, y from y0 - 2
     S* ftile = reinterpret_cast<S*>(smem + L::OFF_F);    // [Q][TY][TX]
     S* gring = reinterpret_cast<S*>(smem + L::OFF_RING);  // [3][Q][TY][TX] (16-bit forms)
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + L::OFF_BAR);  // box, f tile, probe
-    const uint32_t bar_box = smem_addr(&bars[0]), bar_f = smem_addr(&bars[1]), bar_probe = smem_addr(&bars[2]);
+    unsigned long long* bar_probe_p = reinterpret_cast<unsigned long long*>(smem + L::OFF_BAR);
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
@@ -103,47 +84,22 @@ __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
     const int plane = nx * ny;
     const I npad = (I)g.npad;
     if (tid < 2 * Q) refs[tid] = ref_g[tid];
-    if constexpr (kKeepG) {
+    if constexpr (kDev) {
         if (tid == 0) dref = dev_refs_of(ref_g, m);
     }
-    if (tid == 0) {
-        mbar_init(bar_box, NT);
-        mbar_init(bar_f, NT);
-        mbar_init(bar_probe, 1);
+    if (tid == 0 && probe_wait) {
+        mbar_init(smem_addr(bar_probe_p), 1);
         fence_mbar_init();
     }
     const uint64_t keep_l2 = make_l2_evict_last_policy(), drop_l2 = make_l2_evict_first_policy();
     __syncthreads();
+    if (probe_wait) mbar_wait_bounded_n(smem_addr(bar_probe_p), 0, status, max_polls);  // nothing arrives: runs out
 
-    unsigned phase_box = 0, phase_f = 0;
-    bool alive = true;
-    if (probe_wait) mbar_wait_bounded_n(bar_probe, 0, status, max_polls);  // nothing arrives: runs out
-    auto wait = [&](uint32_t bar, unsigned& phase) {
-        if (alive && !mbar_wait_bounded_n(bar, phase, status, max_polls)) {
-            alive = false;
-            cp_async_wait_all();  // this thread's copies land before anything else runs
-        }
-        phase ^= 1u;
-    };
-
-    // Copy assignments, fixed for the whole kernel: thread t takes the
-    // (row, 16-byte column) slot t % NSLOT of a plane and the components
-    // i = t / NSLOT, i + G, i + 2G, ... (G = NT / NSLOT groups of threads), so
-    // a plane's copies cost one address add per component.
-    constexpr int BSLOT = BH * L::BCH, BG = NT / BSLOT;  // box: slots, groups
-    constexpr int FSLOT = TY * L::FCH, FG = NT / FSLOT;  // f tile
-    static_assert(BG >= 1 && FG >= 1, "one copy slot per thread at most");
-    const int bgrp = tid / BSLOT, fgrp = tid / FSLOT;
-    int box_src = 0;
-    uint32_t box_dst = 0;
-    if (bgrp < BG) {
-        const int slot = tid % BSLOT, r = slot / L::BCH, j = slot % L::BCH;
-        int yy = y0 - 2 + r, xx = x0 - CH + j * CH;
-        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
-        xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
-        box_src = yy * nx + xx;
-        box_dst = smem_addr(box + (bgrp * BH + r) * BW + j * CH);
-    }
+    // f tile copies: thread t owns the (row, 16-byte column) slot t % FSLOT of
+    // a plane and the components t / FSLOT, + FG, + 2 FG, ...
+    constexpr int FSLOT = TY * L::FCH, FG = NT / FSLOT;
+    static_assert(FG >= 1, "one copy slot per thread at most");
+    const int fgrp = tid / FSLOT;
     int f_src = 0;
     uint32_t f_dst = 0;
     if (fgrp < FG) {
@@ -151,21 +107,8 @@ __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
         f_src = (y0 + r) * nx + x0 + j * CH;
         f_dst = smem_addr(ftile + (fgrp * TY + r) * TX + j * CH);
     }
-    auto issue_box = [&](int zp) {
-        if (bgrp < BG) {
-            const int zw = zp < 0 ? zp + nz : (zp >= nz ? zp - nz : zp);
-            const S* src = gs + (I)bgrp * npad + ((I)zw * plane + box_src);
-            uint32_t dst = box_dst;
-            for (int i = bgrp; i < Q; i += BG) {
-                cp_async16(dst, src, keep_l2);
-                src += (I)BG * npad;
-                dst += BG * BH * BW * (int)sizeof(S);
-            }
-        }
-        cp_async_arrive_noinc(bar_box);
-    };
     auto issue_f = [&](int zp) {
-        if (fgrp < FG) {
+        if (fgrp < FG && site_ok((long long)zp * plane + f_src + CH - 1, g.n, status)) {
             const S* src = fs + (I)fgrp * npad + ((I)zp * plane + f_src);
             uint32_t dst = f_dst;
             for (int i = fgrp; i < Q; i += FG) {
@@ -174,28 +117,31 @@ __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
                 dst += FG * TY * TX * (int)sizeof(S);
             }
         }
-        cp_async_arrive_noinc(bar_f);
     };
 
-    // phi of plane zp over the tile + 2-halo from the box, into ring slot
-    // `slot`; two x-adjacent sites per thread (216 pairs, one round). Each
-    // site's sum over i keeps its order: phi is the same as in k_step_fused.
-    auto phi_plane = [&](int slot) {
+    // phi of plane zp over the tile + 2-halo into ring slot `slot` (16-bit
+    // forms: psi = phi - Phi), from global memory with evict-last loads (the
+    // collision reads g again two planes later); two x-adjacent sites per
+    // thread from paired loads (216 pairs, one round). Each site's sum over i
+    // keeps its order: phi is the same as in k_step_fused.
+    auto phi_plane = [&](int zp, int slot) {
         constexpr int PW2 = PW / 2;
+        const int zoff = wrap_once(zp, nz) * plane;
         for (int idx = tid; idx < PW2 * PH; idx += NT) {
             const int hx = 2 * (idx % PW2), hy = idx / PW2;
-            const S* b = box + hy * BW + hx + (CH - 2);
-            const bool interior = kKeepG && hx >= 2 && hx < TX + 2 && hy >= 2 && hy < TY + 2;
+            const int sg = zoff + wrap_once(y0 + hy - 2, ny) * nx + wrap_once(x0 + hx - 2, nx);  // even
+            const bool sok = site_ok(sg, g.n, status) && site_ok(sg + 1, g.n, status);
+            const bool interior = kDev && hx >= 2 && hx < TX + 2 && hy >= 2 && hy < TY + 2;
             S* keep = gring + ((size_t)slot * Q * TY + (hy - 2)) * TX + (hx - 2);
             R a0 = R(0), a1 = R(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 if constexpr (sizeof(S) == 4) {
-                    const float2 v = *reinterpret_cast<const float2*>(b + i * (BH * BW));
+                    const float2 v = sok ? ld_l2_hint_pair(gs + (I)i * npad + sg, keep_l2) : make_float2(0.f, 0.f);
                     a0 += v.x;
                     a1 += v.y;
-                } else {  // psi: the sum of the deviations
-                    const unsigned v = *reinterpret_cast<const unsigned*>(b + i * (BH * BW));
+                } else {
+                    const unsigned v = sok ? ld_l2_hint_pair(gs + (I)i * npad + sg, keep_l2) : 0u;
                     if constexpr (P == LD_FP16DEV) {
                         a0 = add_f16(a0, (unsigned short)(v & 0xffffu));
                         a1 = add_f16(a1, (unsigned short)(v >> 16));
@@ -217,7 +163,7 @@ __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
             // the ring holds phi (FP32) or psi = phi - Phi (16-bit forms): the
             // Laplacian is the same, the cubic term takes phi
             const R c = phis[mid][hy][hx];
-            const R ph = kKeepG ? dref.Phi + c : c;
+            const R ph = kDev ? dref.Phi + c : c;
             R lap;
             if constexpr (ISO) {
                 auto nb = [&](int i) { return phis[cz(i) > 0 ? hi : (cz(i) < 0 ? lo : mid)][hy + cy(i)][hx + cx(i)]; };
@@ -233,26 +179,15 @@ __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
     auto ps = [&](int zp) { return (zp - z0 + 2) % 3; };  // phi slot of plane zp (zp >= z0-2)
     auto ms = [&](int zp) { return (zp - z0 + 1) % 3; };  // mu slot of plane zp (zp >= z0-1)
 
-    // Prologue: phi(z0-2..z0+1), mu(z0-1), mu(z0); box of z0+2 in flight.
-    issue_box(z0 - 2);
-    wait(bar_box, phase_box);
-    phi_plane(ps(z0 - 2));
-    __syncthreads();  // box free
-    issue_box(z0 - 1);
-    wait(bar_box, phase_box);
-    phi_plane(ps(z0 - 1));
+    // Prologue: phi(z0-2..z0+1), mu(z0-1), mu(z0).
+    phi_plane(z0 - 2, ps(z0 - 2));
+    phi_plane(z0 - 1, ps(z0 - 1));
+    phi_plane(z0, ps(z0));
     __syncthreads();
-    issue_box(z0);
-    wait(bar_box, phase_box);
-    phi_plane(ps(z0));
-    __syncthreads();  // phi(z0-2..z0) visible; box free
-    issue_box(z0 + 1);
     mu_plane(ms(z0 - 1), ps(z0 - 2), ps(z0 - 1), ps(z0));
-    wait(bar_box, phase_box);
-    __syncthreads();  // phi(z0+1) reuses the slot mu(z0-1) read
-    phi_plane(ps(z0 + 1));
-    __syncthreads();  // phi(z0+1) visible; box free
-    issue_box(z0 + 2);
+    __syncthreads();  // phi(z0+1) reuses the slot mu(z0-1) just read
+    phi_plane(z0 + 1, ps(z0 + 1));
+    __syncthreads();
     mu_plane(ms(z0), ps(z0 - 1), ps(z0), ps(z0 + 1));
 
     const int x = x0 + tx, y = y0 + ty;
@@ -262,26 +197,26 @@ __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
     for (int k = z0; k < z0 + zc; ++k) {
         const int z = k;  // zc divides nz: k < nz
         const int s = z * plane + y * nx + x;
+        const bool cok = site_ok(s, g.n, status);
         // FP32: the collision's g re-read (an L2 hit) issued before the
         // passes, so that its latency overlaps them.
         S gpre[Q];
-        if constexpr (kEarlyG) {
+        if constexpr (!kDev) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) gpre[i] = ld_l2_hint_now(gs + (I)i * npad + s, drop_l2);
+            for (int i = 0; i < Q; ++i) gpre[i] = cok ? ld_l2_hint_now(gs + (I)i * npad + s, drop_l2) : S(0);
         }
         __syncthreads();  // collision k-1 done with the f tile and the ring slots of phi(k-1), mu(k-2)
         issue_f(k);
-        wait(bar_box, phase_box);
-        phi_plane(ps(k + 2));
-        __syncthreads();  // phi(k+2) visible; box free
-        if (k + 3 <= z0 + zc + 1) issue_box(k + 3);
+        cp_async_commit();
+        phi_plane(k + 2, ps(k + 2));
+        __syncthreads();
         mu_plane(ms(k + 1), ps(k), ps(k + 1), ps(k + 2));
-        wait(bar_f, phase_f);
-        __syncthreads();  // mu(k+1) visible
+        cp_async_wait_group0();  // this thread's f copies have landed
+        __syncthreads();         // mu(k+1) and every thread's f copies visible
 
         const int ozp = z + 1 == nz ? (1 - nz) * plane : plane, ozm = z == 0 ? (nz - 1) * plane : -plane;
         const R ring_c = phis[ps(k)][ty + 2][tx + 2];  // phi, or psi in the 16-bit forms
-        const R ph = kKeepG ? dref.Phi + ring_c : ring_c;
+        const R ph = kDev ? dref.Phi + ring_c : ring_c;
         const int mc = ms(k);
         const R muc = mus[mc][ty + 1][tx + 1];
         R gmx, gmy, gmz;
@@ -295,7 +230,7 @@ __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
             gmz = R(0.5) * (mus[ms(k + 1)][ty + 1][tx + 1] - mus[ms(k - 1)][ty + 1][tx + 1]);
         }
         const R Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
-        if (phi_out) {  // fields of the source state, for the adjoint
+        if (phi_out && cok) {  // fields of the source state, for the adjoint
             phi_out[s] = ph;
             mu_out[s] = muc;
         }
@@ -308,7 +243,7 @@ __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
 
         R f[Q];
         R ux, uy, uz;
-        if constexpr (kKeepG) {  // deviation space
+        if constexpr (kDev) {  // deviation space
             R delta = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -332,33 +267,38 @@ __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const R ref = kKeepG ? R(0) : refs[i];  // deviations are stored as they are
+            const R ref = kDev ? R(0) : refs[i];  // deviations are stored as they are
+            const int d = dest(i);
+            S v;
             if constexpr (SR)
-                __stcs(fd + (I)i * npad + dest(i), Prec<P>::encode_sr(f[i], ref, sr_key(sr, sr_st, 0, i, sr_w)));
+                v = Prec<P>::encode_sr(f[i], ref, sr_key(sr, sr_st, 0, i, sr_w));
             else
-                __stcs(fd + (I)i * npad + dest(i), Prec<P>::encode(f[i], ref));
+                v = Prec<P>::encode(f[i], ref);
+            if (site_ok(d, g.n, status)) __stcs(fd + (I)i * npad + d, v);
         }
 
         R gg[Q];
-        if constexpr (kKeepG) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) gg[i] = to_float(gring[((size_t)ps(k) * Q + i) * (TY * TX) + ty * TX + tx]);
-            collide_g_dev(gg, ring_c, ph, muc - dref.muP, ux, uy, uz, m, dref);
-        } else {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) gg[i] = Prec<P>::decode(gpre[i], refs[Q + i]);
-            collide_g(gg, ph, muc, ux, uy, uz, m);
-        }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const R ref = kKeepG ? R(0) : refs[Q + i];
+            const S v = kDev ? gring[((size_t)ps(k) * Q + i) * (TY * TX) + ty * TX + tx] : gpre[i];
+            gg[i] = kDev ? to_float(v) : Prec<P>::decode(v, refs[Q + i]);
+        }
+        if constexpr (kDev)
+            collide_g_dev(gg, ring_c, ph, muc - dref.muP, ux, uy, uz, m, dref);
+        else
+            collide_g(gg, ph, muc, ux, uy, uz, m);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const R ref = kDev ? R(0) : refs[Q + i];
+            const int d = dest(i);
+            S v;
             if constexpr (SR)
-                __stcs(gd + (I)i * npad + dest(i), Prec<P>::encode_sr(gg[i], ref, sr_key(sr, sr_st, 1, i, sr_w)));
+                v = Prec<P>::encode_sr(gg[i], ref, sr_key(sr, sr_st, 1, i, sr_w));
             else
-                __stcs(gd + (I)i * npad + dest(i), Prec<P>::encode(gg[i], ref));
+                v = Prec<P>::encode(gg[i], ref);
+            if (site_ok(d, g.n, status)) __stcs(gd + (I)i * npad + d, v);
         }
     }
-    cp_async_wait_all();  // nothing of this CTA's is still in flight when it exits
 }
 
 template <int P>

@@ -12,6 +12,7 @@ built or loaded, every call raises.
 
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import threading
 
@@ -97,19 +98,39 @@ _SIGNATURES = {
 }
 
 
+def _load(path):
+    handle = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(handle, name)
+        fn.restype = res
+        fn.argtypes = args
+    return handle
+
+
 def lib():
     """Load libld.so (building it first if it is missing or stale)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
-            handle = ctypes.CDLL(path)
-            for name, (res, args) in _SIGNATURES.items():
-                fn = getattr(handle, name)
-                fn.restype = res
-                fn.argtypes = args
-            _lib = handle
+            _lib = _load(_build.build())
         return _lib
+
+
+@contextlib.contextmanager
+def debug_library():
+    """Within the block every call goes to the bounds-checked debug build
+    (libld_debug.so, built on first use): its step kernels report a site
+    index outside the lattice through ld_check instead of faulting. Contexts
+    created inside the block belong to it."""
+    global _lib
+    release = lib()
+    with _lock:
+        _lib = _load(_build.build(debug=True))
+    try:
+        yield _lib
+    finally:
+        with _lock:
+            _lib = release
 
 
 def _ptr(t):
