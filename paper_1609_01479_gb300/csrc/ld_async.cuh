@@ -81,6 +81,12 @@ __device__ __forceinline__ unsigned ld_l2_hint_pair(const void* p, uint64_t pol)
     asm("ld.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
     return v;
 }
+// The same, issued where it is written (volatile), to overlap its latency.
+__device__ __forceinline__ unsigned ld_l2_hint_pair_now(const void* p, uint64_t pol) {
+    unsigned v;
+    asm volatile("ld.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;

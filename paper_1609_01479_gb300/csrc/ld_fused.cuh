@@ -317,8 +317,8 @@ constexpr int kTY = 8;
 // prologue worth about two collided planes (four extra phi planes and the
 // pipeline start); pick the divisor of nz among 64..4 that minimises
 // waves x (planes per CTA + 2).
-int choose_zc(int nx, int ny, int nz, int num_sms = 152, int per_sm = 2) {
-    const long long cols = (long long)(nx / kTX) * (ny / kTY);
+int choose_zc_rows(int nx, int ny, int nz, int rows, int num_sms = 152, int per_sm = 2) {
+    const long long cols = (long long)(nx / kTX) * (ny / rows);
     const long long slots = (long long)per_sm * num_sms;
     int best = 0;
     long long best_cost = 0;
@@ -332,6 +332,9 @@ int choose_zc(int nx, int ny, int nz, int num_sms = 152, int per_sm = 2) {
         }
     }
     return best;
+}
+int choose_zc(int nx, int ny, int nz, int num_sms = 152, int per_sm = 2) {
+    return choose_zc_rows(nx, ny, nz, kTY, num_sms, per_sm);
 }
 
 template <int P, class I, bool ISO, bool SR>

@@ -1,6 +1,7 @@
 // FP32, FP16-deviation and BF16-deviation instantiations of the step
 // kernels, and the launches that do not depend on the precision.
 #include "ld_fused.cuh"
+#include "ld_fused2.cuh"
 #include "ld_generic.cuh"
 #include "ld_staged.cuh"
 #include "ld_adjoint.cuh"
@@ -30,6 +31,11 @@ cudaError_t totals(ld_ctx* c, double* t) { LD_LP_DISPATCH(totals_p, c, t); }
 cudaError_t decode(ld_ctx* c, double* f, double* g) { LD_LP_DISPATCH(decode_p, c, f, g); }
 cudaError_t encode(ld_ctx* c, const double* f, const double* g) { LD_LP_DISPATCH(encode_p, c, f, g); }
 cudaError_t step_fused_regs(ld_ctx* c, const void* src, void* dst, void* fields) {
+    // the 16-bit forms, rounding to nearest: two sites per thread, packed FP32
+    if (kPairs16 && c->prm.rounding == LD_ROUND_NEAREST) {
+        if (c->prec == LD_FP16DEV) return step_fused2_p<LD_FP16DEV>(c, src, dst, fields);
+        if (c->prec == LD_BF16DEV) return step_fused2_p<LD_BF16DEV>(c, src, dst, fields);
+    }
     LD_LP_DISPATCH(step_fused_p, c, src, dst, fields);
 }
 cudaError_t step_staged(ld_ctx* c, const void* src, void* dst, void* fields) {
