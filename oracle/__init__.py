@@ -25,6 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ld_oracle.cpp")
+_LC_SRC = os.path.join(_HERE, "lc_oracle.cpp")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -44,13 +45,14 @@ FORCES = {"potential": 0.0, "stress": 1.0}
 
 
 def build(force: bool = False) -> str:
-    """Compile ld_oracle.cpp into _build/liboracle.so (g++, -O2, OpenMP)."""
+    """Compile ld_oracle.cpp and lc_oracle.cpp into _build/liboracle.so (g++, -O2, OpenMP)."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_LC_SRC))
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-           _SRC, "-o", tmp]
+           _SRC, _LC_SRC, "-o", tmp]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -82,8 +84,15 @@ def _load():
         lib.orc_step_tl.argtypes = [i, i, i, P, P, P, P, P, P, i]
         lib.orc_loss_jvp.argtypes = [i, i, i, P, P, P, P, P, i, P, P]
         lib.orc_stress.argtypes = [i, i, i, P, P, P]
+        lib.orc_lc_field.argtypes = [i, i, i, P, P, P, P]
+        lib.orc_lc_corotation.argtypes = [P, P, P, P]
+        lib.orc_lc_update.argtypes = [i, i, i, P, P, P, P, P]
+        lib.orc_lc_macros.argtypes = [i, i, i, P, P, P, P, P, P]
+        lib.orc_lc_init.argtypes = [i, i, i, P, P, P, P]
+        lib.orc_lc_step.argtypes = [i, i, i, P, P, P, i]
         for name in ("orc_laplacian", "orc_gradient", "orc_propagate", "orc_init", "orc_step",
-                     "orc_macros", "orc_step_tl", "orc_loss_jvp", "orc_stress"):
+                     "orc_macros", "orc_step_tl", "orc_loss_jvp", "orc_stress", "orc_lc_field", "orc_lc_update",
+                     "orc_lc_macros", "orc_lc_init", "orc_lc_step"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -267,3 +276,76 @@ def loss(phi0, phi_target, prm, nsteps):
     f, g = step(f, g, prm, nsteps)
     phi_T = g.sum(axis=0)
     return float(((phi_T - phi_target) ** 2).sum())
+
+
+# ---------------------------------------------------------------------------
+# Liquid crystal (lc_oracle.cpp): Landau-de Gennes Q-tensor, Beris-Edwards
+# update, chemical stress coupled to the D3Q19 fluid. Q is held as its five
+# independent components (xx, xy, xz, yy, yz), shaped (5, nz, ny, nx).
+LC_PARAM_NAMES = ("A0", "gamma", "kappa", "Gamma", "xi", "tau_f", "rho0")
+LC_DEFAULT_PARAMS = dict(A0=0.01, gamma=3.0, kappa=0.01, Gamma=0.3, xi=0.7, tau_f=1.0, rho0=1.0)
+
+
+def lc_param_vector(**overrides) -> np.ndarray:
+    p = dict(LC_DEFAULT_PARAMS)
+    for k, v in overrides.items():
+        if k not in p:
+            raise KeyError(k)
+        p[k] = float(v)
+    return np.array([p[k] for k in LC_PARAM_NAMES], dtype=np.float64)
+
+
+def lc_field(q, prm):
+    """Molecular field H (5, ...) and chemical stress sigma (9, ..., row-major ab) of Q."""
+    q = _f64(q)
+    _, nz, ny, nx = q.shape
+    h = np.zeros((5,) + q.shape[1:])
+    sigma = np.zeros((9,) + q.shape[1:])
+    _check(_load().orc_lc_field(nx, ny, nz, _ptr(_f64(prm)), _ptr(q), _ptr(h), _ptr(sigma)), "lc_field")
+    return h, sigma
+
+
+def lc_corotation(W, Q, prm):
+    """S(W, Q) for full 3x3 W (W_ab = d_b u_a) and Q."""
+    out = np.zeros(9)
+    _load().orc_lc_corotation(_ptr(_f64(prm)), _ptr(_f64(np.asarray(W).reshape(9))),
+                              _ptr(_f64(np.asarray(Q).reshape(9))), _ptr(out))
+    return out.reshape(3, 3)
+
+
+def lc_update(q, u, h, prm):
+    """Q(t+1) from Q, a velocity field u (3, ...) and H (5, ...)."""
+    q = _f64(q)
+    _, nz, ny, nx = q.shape
+    out = np.zeros_like(q)
+    _check(_load().orc_lc_update(nx, ny, nz, _ptr(_f64(prm)), _ptr(q), _ptr(_f64(u)), _ptr(_f64(h)), _ptr(out)),
+           "lc_update")
+    return out
+
+
+def lc_macros(f, q, prm):
+    """rho, u = (j + F/2)/rho and F = div sigma of the state (f, Q)."""
+    f = _f64(f)
+    shp = f.shape[1:]
+    nz, ny, nx = shp
+    rho, u, F = np.zeros(shp), np.zeros((3,) + shp), np.zeros((3,) + shp)
+    _check(_load().orc_lc_macros(nx, ny, nz, _ptr(_f64(prm)), _ptr(f), _ptr(_f64(q)), _ptr(rho), _ptr(u), _ptr(F)),
+           "lc_macros")
+    return dict(rho=rho, u=u, force=F)
+
+
+def lc_init(shape, prm, rho=None, u=None):
+    """f = feq(rho, u) (rho0 and rest where not given) on a (nz, ny, nx) lattice."""
+    nz, ny, nx = shape
+    f = np.zeros((Q, nz, ny, nx))
+    _check(_load().orc_lc_init(nx, ny, nz, _ptr(_f64(prm)), _ptr(_f64(rho)), _ptr(_f64(u)), _ptr(f)), "lc_init")
+    return f
+
+
+def lc_step(f, q, prm, nsteps=1):
+    """Advance copies of (f, Q) by nsteps coupled steps."""
+    f = np.array(f, dtype=np.float64, order="C", copy=True)
+    q = np.array(q, dtype=np.float64, order="C", copy=True)
+    _, nz, ny, nx = f.shape
+    _check(_load().orc_lc_step(nx, ny, nz, _ptr(_f64(prm)), _ptr(f), _ptr(q), int(nsteps)), "lc_step")
+    return f, q
