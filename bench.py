@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-lc", action="store_true", help="skip the liquid-crystal step line")
+    ap.add_argument("--lc-size", type=int, default=256, help="lattice edge of the liquid-crystal step line")
     ap.add_argument("--no-per-size", action="store_true",
                     help="skip the FP32 line at 256^3 (the size of the FP32 roofline target)")
     ap.add_argument("--stencil", type=int, default=7, choices=[7, 19],
@@ -422,6 +424,31 @@ def time_adjoint(args, ld, phi_dev, precision, steps=40, every=10):
     return out
 
 
+def time_lc(args, ld, n, precision):
+    """The liquid-crystal step (Q-tensor + D3Q19 fluid, three launches) on an
+    n^3 lattice from a disordered seeded Q, at rest: args.warmup untimed
+    steps, then args.steps timed with CUDA events on the launching stream."""
+    import torch
+
+    from paper_1609_01479_gb300 import inputs
+
+    stream = torch.cuda.current_stream()
+    sim = ld.LcSim(n, n, n, precision=precision, stream=stream.cuda_stream)
+    sim.init(torch.from_numpy(inputs.random_q(n, n, n, seed=SEED)).to("cuda"))
+    sim.step(args.warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return ms
+
+
 def cpu_baseline(sample_edge=96, sample_steps=20):
     """The FP64 oracle, as it stands, on the host cores: MLUPS on a bounded
     sample (a sample_edge^3 lattice of the same workload, sample_steps steps)."""
@@ -562,6 +589,20 @@ def main():
                "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
                "what": f"pinned phi0 H2D + ld_init + {args.steps} ld_step + ld_moments(phi) + D2H, one run"}
     adj = None if args.no_adjoint else time_adjoint(args, ld, phi_dev, primary)
+    # The liquid-crystal step (the paper's Ludwig test case), 256^3 by default: its
+    # state is f (19 values) and Q (5 values) per site, read and written once
+    # a step at the least: 48 x (bytes per value); the three launches also
+    # write and read H (5), sigma (9) and u (3), 92 values in all.
+    lc = {}
+    if not args.no_lc:
+        n_lc = args.lc_size
+        for prec in ("fp32", "fp64"):
+            ms = max_over_ranks(world, time_lc(args, ld, n_lc, prec))
+            bps = 48 * BYTES_PER_VALUE[prec]
+            gbs = n_lc ** 3 * bps / (ms * 1e-3) / 1e9
+            lc[prec] = {"lattice": [n_lc] * 3, "mlups": world * n_lc ** 3 / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                        "state_bytes_per_site": bps, "launch_bytes_per_site": 92 * BYTES_PER_VALUE[prec],
+                        "state_gbs": gbs, "roofline_frac_of_state": gbs / peak}
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline()
@@ -595,6 +636,7 @@ def main():
         "cpu_baseline": cpu,
         "per_precision": {p: {k: v for k, v in r.items() if k not in ("clocks",)} for p, r in results.items()},
         "per_size": per_size,
+        "lc": lc,
         "adjoint_forward_ratio": None if adj is None else adj["backward_ms_per_step"] / P["ms_per_step"],
         "adjoint": adj,
     }

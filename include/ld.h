@@ -352,6 +352,53 @@ int ld_totals_static(int nx, int ny, int nz, const double* f, const double* g, d
  * ld_last_error(NULL). */
 int ld_probe_fp64_rate(int op, int blocks, int iters, double* sink, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Liquid crystal: the paper's Ludwig test case (Sec. 2.1.1: "Order Parameter
+ * Gradients", "Chemical stress", "Collision", "Propagation", "LC Update",
+ * "Advection"; the paper cites the Beris-Edwards model and the Landau-de
+ * Gennes free energy without printing them). A symmetric traceless Q-tensor,
+ * stored as its five components (xx, xy, xz, yy, yz; zz = -xx - yy), on the
+ * same periodic D3Q19 lattice as a fluid of distributions f. One step:
+ *   H_ab = -A0 (1 - gamma/3) Q_ab + A0 gamma (Q_ac Q_cb - delta_ab Q_cd Q_cd/3)
+ *          - A0 gamma (Q_cd Q_cd) Q_ab + kappa lap(Q_ab)        (molecular field)
+ *   sigma_ab = f delta_ab - kappa d_a Q_cd d_b Q_cd - xi H_ac (Q_cb + delta_cb/3)
+ *          - xi (Q_ac + delta_ac/3) H_cb + 2 xi (Q_ab + delta_ab/3) Q_cd H_cd
+ *          + Q_ac H_cb - H_ac Q_cb                                  (chemical stress)
+ *   with f = A0/2 (1 - gamma/3) Q:Q - A0 gamma/3 tr(Q^3) + A0 gamma/4 (Q:Q)^2
+ *          + kappa/2 |grad Q|^2;
+ *   F_a = d_b sigma_ab, u = (j + F/2)/rho, BGK + Guo collision of f, propagation;
+ *   Q <- Q + Gamma H + S(W, Q) - u.grad(Q), W_ab = d_b u_a,
+ *   S = (xi D + Om)(Q + I/3) + (Q + I/3)(xi D - Om) - 2 xi (Q + I/3) tr(Q W),
+ * d the central difference, lap the 7-point Laplacian, advection first-order
+ * upwind, dt = 1. FP64 or FP32 storage and arithmetic. The same conventions
+ * as the binary-fluid calls: device pointers, caller-owned workspace,
+ * stream-ordered, error codes with messages from ld_last_error(NULL). */
+typedef struct {
+    double A0, gamma, kappa; /* Landau-de Gennes bulk scale, ordering parameter, elastic constant */
+    double Gamma, xi;        /* rotational diffusion constant, flow-aligning parameter */
+    double tau_f, rho0;      /* fluid relaxation time (> 1/2), reference density */
+    int precision;           /* LD_FP64 or LD_FP32 */
+} lc_params;
+typedef struct lc_ctx lc_ctx;
+
+/* Workspace of an nx*ny*nz liquid-crystal lattice (each dim >= 3); 0 for
+ * invalid arguments. */
+size_t lc_workspace_bytes(int nx, int ny, int nz, const lc_params* params);
+/* Create a context over a 256-byte aligned device workspace of at least
+ * lc_workspace_bytes() bytes, on cuda_stream. */
+int lc_create(int nx, int ny, int nz, const lc_params* params, void* dev_workspace, size_t bytes, void* cuda_stream,
+              lc_ctx** out);
+/* Initial state: Q from device double[5][N]; f = feq(rho, u) with rho
+ * double[N] (NULL: rho0) and u double[3][N] (NULL: rest). */
+int lc_init(lc_ctx* ctx, const double* q, const double* rho, const double* u);
+/* Advance nsteps >= 0 coupled steps (three launches each). */
+int lc_step(lc_ctx* ctx, int nsteps);
+/* Current state as device doubles, each output may be NULL: q [5][N], rho
+ * [N], u [3][N] (the velocity (j + F/2)/rho with the force of the current
+ * Q), h [5][N] (molecular field), f [19][N]. */
+int lc_fields(lc_ctx* ctx, double* q, double* rho, double* u, double* h, double* f);
+int lc_destroy(lc_ctx* ctx);
+
 /* Message for an error code, and the last error recorded on a context. */
 const char* ld_strerror(int code);
 const char* ld_last_error(const ld_ctx* ctx);

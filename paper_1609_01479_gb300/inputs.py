@@ -77,3 +77,11 @@ def shear_wave_u(nx: int, ny: int, nz: int, u0: float, mode: int = 1) -> np.ndar
     u = np.zeros((3, nz, ny, nx))
     u[0] = ux[None, :, None]
     return u
+
+
+def random_q(nx: int, ny: int, nz: int, seed: int, amplitude: float = 0.15) -> np.ndarray:
+    """Five Q-tensor components (xx, xy, xz, yy, yz) per site, each uniform in
+    [-amplitude, amplitude) from its own seed (seed, seed + 1, ...), shaped
+    (5, nz, ny, nx): a disordered liquid-crystal start."""
+    n = nx * ny * nz
+    return np.stack([(amplitude * (2.0 * uniform01(n, seed + k) - 1.0)).reshape(nz, ny, nx) for k in range(5)])

@@ -47,6 +47,12 @@ class LdParams(ctypes.Structure):
                 ("magic", ctypes.c_double), ("rounding", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
+class LcParams(ctypes.Structure):
+    _fields_ = [("A0", ctypes.c_double), ("gamma", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("Gamma", ctypes.c_double), ("xi", ctypes.c_double), ("tau_f", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
 class LdError(RuntimeError):
     def __init__(self, code: int, where: str, message: str):
         super().__init__(f"{where} failed ({code}): {message}")
@@ -93,6 +99,13 @@ _SIGNATURES = {
     "ld_adjoint_set": (ctypes.c_int, [_VP, _VP, _VP]),
     "ld_totals_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "ld_probe_fp64_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    "lc_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(LcParams)]),
+    "lc_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(LcParams), _VP,
+                                 ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+    "lc_init": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "lc_step": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "lc_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "lc_destroy": (ctypes.c_int, [_VP]),
     "ld_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ld_last_error": (ctypes.c_char_p, [_VP]),
 }
@@ -345,6 +358,92 @@ def ld_probe_fp64_rate(op: int, blocks: int, iters: int, sink, stream=None):
     if rc != LD_OK:
         raise LdError(rc, "ld_probe_fp64_rate", lib().ld_last_error(None).decode(errors="replace"))
     return rc
+
+
+# ---------------------------------------------------------------------------
+# Liquid crystal (see ld.h): same-named wrappers and LcSim.
+
+def _lc_call(name, *args):
+    rc = getattr(lib(), name)(*args)
+    if rc != LD_OK:
+        raise LdError(rc, name, lib().ld_last_error(None).decode(errors="replace"))
+    return rc
+
+
+def make_lc_params(A0=0.01, gamma=3.0, kappa=0.01, Gamma=0.3, xi=0.7, tau_f=1.0, rho0=1.0,
+                   precision="fp32") -> LcParams:
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return LcParams(A0, gamma, kappa, Gamma, xi, tau_f, rho0, prec)
+
+
+def lc_workspace_bytes(nx, ny, nz, params: LcParams) -> int:
+    return int(lib().lc_workspace_bytes(nx, ny, nz, ctypes.byref(params)))
+
+
+def lc_create(nx, ny, nz, params: LcParams, workspace, stream=None):
+    out = ctypes.c_void_p()
+    s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream(workspace.device).cuda_stream)
+    _lc_call("lc_create", nx, ny, nz, ctypes.byref(params), _ptr(workspace),
+             workspace.numel() * workspace.element_size(), s, ctypes.byref(out))
+    return out
+
+
+def lc_init(ctx, q, rho=None, u=None):
+    return _lc_call("lc_init", ctx, _ptr(q), _ptr(rho), _ptr(u))
+
+
+def lc_step(ctx, nsteps: int):
+    return _lc_call("lc_step", ctx, int(nsteps))
+
+
+def lc_fields(ctx, q=None, rho=None, u=None, h=None, f=None):
+    return _lc_call("lc_fields", ctx, _ptr(q), _ptr(rho), _ptr(u), _ptr(h), _ptr(f))
+
+
+def lc_destroy(ctx):
+    return lib().lc_destroy(ctx)
+
+
+class LcSim:
+    """A liquid-crystal lattice with its torch-owned workspace. Q is given
+    and returned as float64 CUDA tensors (5, nz, ny, nx) of the components
+    xx, xy, xz, yy, yz."""
+
+    def __init__(self, nx, ny, nz, precision="fp32", device="cuda", stream=None, **model):
+        self.shape = (nz, ny, nx)
+        self.device = torch.device(device)
+        self.params = make_lc_params(precision=precision, **model)
+        nbytes = lc_workspace_bytes(nx, ny, nz, self.params)
+        if nbytes == 0:
+            raise LdError(LD_EINVAL, "lc_workspace_bytes", "invalid lattice size or parameters")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.ctx = lc_create(nx, ny, nz, self.params, self.workspace, stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, q, rho=None, u=None):
+        conv = lambda t: None if t is None else torch.as_tensor(t, dtype=torch.float64,  # noqa: E731
+                                                                 device=self.device).contiguous()
+        self._inputs = (conv(q), conv(rho), conv(u))
+        lc_init(self.ctx, *self._inputs)
+
+    def step(self, nsteps=1):
+        lc_step(self.ctx, nsteps)
+
+    def fields(self):
+        mk = lambda *lead: torch.empty(*lead, *self.shape, dtype=torch.float64, device=self.device)  # noqa: E731
+        out = dict(q=mk(5), rho=mk(), u=mk(3), h=mk(5), f=mk(Q))
+        lc_fields(self.ctx, out["q"], out["rho"], out["u"], out["h"], out["f"])
+        return out
 
 
 def ld_strerror(code: int) -> str:

@@ -16,7 +16,7 @@ HEADER = os.path.join(ROOT, "include", "ld.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"\b(ld_[a-z_]+)\s*\(", text)
+    names = re.findall(r"\b((?:ld|lc)_[a-z0-9_]+)\s*\(", text)
     return sorted(set(names))
 
 
@@ -137,3 +137,16 @@ def test_static_totals_wrapper_checks_buffers_before_any_launch(ld):
         ld.ld_totals_static(16, 16, 16, f.float(), f, out)
     with pytest.raises(TypeError):
         ld.ld_totals_static(16, 16, 16, f.numpy(), f, out)
+
+
+def test_lc_workspace_bytes_validates_its_arguments(ld):
+    ws = ld.lc_workspace_bytes
+    p = ld.make_lc_params(precision="fp32")
+    b = ws(8, 8, 8, p)
+    n = 8 * 8 * 8
+    # f ping-pong, Q ping-pong, H, sigma, u: (2*19 + 2*5 + 5 + 9 + 3) values per site
+    assert b >= 65 * n * 4 and b % 256 == 0
+    assert ws(8, 8, 8, ld.make_lc_params(precision="fp64")) >= 65 * n * 8
+    assert ws(2, 8, 8, p) == 0
+    assert ws(8, 8, 8, ld.make_lc_params(precision="fp16dev")) == 0
+    assert ws(8, 8, 8, ld.make_lc_params(tau_f=0.5)) == 0
