@@ -425,9 +425,10 @@ def time_adjoint(args, ld, phi_dev, precision, steps=40, every=10):
 
 
 def time_lc(args, ld, n, precision):
-    """The liquid-crystal step (Q-tensor + D3Q19 fluid, three launches) on an
-    n^3 lattice from a disordered seeded Q, at rest: args.warmup untimed
-    steps, then args.steps timed with CUDA events on the launching stream."""
+    """The liquid-crystal step (Q-tensor + D3Q19 fluid, the context's own
+    step kernel) on an n^3 lattice from a disordered seeded Q, at rest:
+    args.warmup untimed steps, then args.steps timed with CUDA events on the
+    launching stream. Returns (ms per step, step kernel)."""
     import torch
 
     from paper_1609_01479_gb300 import inputs
@@ -443,10 +444,11 @@ def time_lc(args, ld, n, precision):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    kernel = sim.kernel
     sim.close()
     del sim
     torch.cuda.empty_cache()
-    return ms
+    return ms, kernel
 
 
 def cpu_baseline(sample_edge=96, sample_steps=20):
@@ -591,18 +593,27 @@ def main():
     adj = None if args.no_adjoint else time_adjoint(args, ld, phi_dev, primary)
     # The liquid-crystal step (the paper's Ludwig test case), 256^3 by default: its
     # state is f (19 values) and Q (5 values) per site, read and written once
-    # a step at the least: 48 x (bytes per value); the three launches also
-    # write and read H (5), sigma (9) and u (3), 92 values in all.
+    # a step at the least: 48 values. What the launches move on top:
+    #   fused (z-marching field + collision, then the Q update): Q read once
+    #     more (5), u written and read (6): 59 values;
+    #   generic (three per-site launches): Q read once more (5), H (10),
+    #     sigma (18) and u (6) written and read: 87 values.
     lc = {}
     if not args.no_lc:
         n_lc = args.lc_size
+        launch_values = {"fused": 59, "generic": 87}
         for prec in ("fp32", "fp64"):
-            ms = max_over_ranks(world, time_lc(args, ld, n_lc, prec))
+            ms, kernel = time_lc(args, ld, n_lc, prec)
+            ms = max_over_ranks(world, ms)
             bps = 48 * BYTES_PER_VALUE[prec]
+            lbps = launch_values[kernel] * BYTES_PER_VALUE[prec]
             gbs = n_lc ** 3 * bps / (ms * 1e-3) / 1e9
-            lc[prec] = {"lattice": [n_lc] * 3, "mlups": world * n_lc ** 3 / (ms * 1e-3) / 1e6, "ms_per_step": ms,
-                        "state_bytes_per_site": bps, "launch_bytes_per_site": 92 * BYTES_PER_VALUE[prec],
-                        "state_gbs": gbs, "roofline_frac_of_state": gbs / peak}
+            lgbs = n_lc ** 3 * lbps / (ms * 1e-3) / 1e9
+            lc[prec] = {"lattice": [n_lc] * 3, "kernel": kernel,
+                        "mlups": world * n_lc ** 3 / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                        "state_bytes_per_site": bps, "launch_bytes_per_site": lbps,
+                        "state_gbs": gbs, "roofline_frac_of_state": gbs / peak,
+                        "launch_gbs": lgbs, "roofline_frac_of_launch_bytes": lgbs / peak}
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline()

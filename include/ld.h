@@ -372,12 +372,21 @@ int ld_probe_fp64_rate(int op, int blocks, int iters, double* sink, void* cuda_s
  * d the central difference, lap the 7-point Laplacian, advection first-order
  * upwind, dt = 1. FP64 or FP32 storage and arithmetic. The same conventions
  * as the binary-fluid calls: device pointers, caller-owned workspace,
- * stream-ordered, error codes with messages from ld_last_error(NULL). */
+ * stream-ordered, error codes with messages from ld_last_error(NULL).
+ * Step kernels (lc_params.kernel):
+ *   LD_KERNEL_GENERIC: three launches, one thread per site (H and sigma;
+ *     F, u, collision and push; Q update); any lattice.
+ *   LD_KERNEL_FUSED: two launches. A z-marching launch keeps Q and sigma of
+ *     three planes in shared memory and collides and pushes f, writing only f
+ *     and u; the Q update recomputes H from Q. nx % 32 == 0, ny % 8 == 0.
+ *   LD_KERNEL_AUTO: FUSED for FP32 where the lattice admits it, else GENERIC.
+ * Both give the same values: the same operations in the same order. */
 typedef struct {
     double A0, gamma, kappa; /* Landau-de Gennes bulk scale, ordering parameter, elastic constant */
     double Gamma, xi;        /* rotational diffusion constant, flow-aligning parameter */
     double tau_f, rho0;      /* fluid relaxation time (> 1/2), reference density */
     int precision;           /* LD_FP64 or LD_FP32 */
+    int kernel;              /* LD_KERNEL_AUTO, LD_KERNEL_GENERIC or LD_KERNEL_FUSED */
 } lc_params;
 typedef struct lc_ctx lc_ctx;
 
@@ -385,14 +394,19 @@ typedef struct lc_ctx lc_ctx;
  * invalid arguments. */
 size_t lc_workspace_bytes(int nx, int ny, int nz, const lc_params* params);
 /* Create a context over a 256-byte aligned device workspace of at least
- * lc_workspace_bytes() bytes, on cuda_stream. */
+ * lc_workspace_bytes() bytes, on cuda_stream. LD_EINVAL for kernel
+ * LD_KERNEL_FUSED on a lattice that does not admit it. */
 int lc_create(int nx, int ny, int nz, const lc_params* params, void* dev_workspace, size_t bytes, void* cuda_stream,
               lc_ctx** out);
 /* Initial state: Q from device double[5][N]; f = feq(rho, u) with rho
  * double[N] (NULL: rho0) and u double[3][N] (NULL: rest). */
 int lc_init(lc_ctx* ctx, const double* q, const double* rho, const double* u);
-/* Advance nsteps >= 0 coupled steps (three launches each). */
+/* Advance nsteps >= 0 coupled steps (three launches each with
+ * LD_KERNEL_GENERIC, two with LD_KERNEL_FUSED). */
 int lc_step(lc_ctx* ctx, int nsteps);
+/* The step kernel a context runs (LD_KERNEL_AUTO resolved):
+ * LD_KERNEL_GENERIC or LD_KERNEL_FUSED; LD_EINVAL for a NULL context. */
+int lc_step_kernel(const lc_ctx* ctx);
 /* Current state as device doubles, each output may be NULL: q [5][N], rho
  * [N], u [3][N] (the velocity (j + F/2)/rho with the force of the current
  * Q), h [5][N] (molecular field), f [19][N]. */

@@ -16,6 +16,8 @@ long long npad_of(long long n) { return (n + 63) / 64 * 64; }
 bool lc_params_ok(const lc_params* p, const char** why) {
     if (!p) return *why = "params is NULL", false;
     if (p->precision != LD_FP64 && p->precision != LD_FP32) return *why = "precision must be LD_FP64 or LD_FP32", false;
+    if (p->kernel != LD_KERNEL_AUTO && p->kernel != LD_KERNEL_GENERIC && p->kernel != LD_KERNEL_FUSED)
+        return *why = "kernel must be LD_KERNEL_AUTO, LD_KERNEL_GENERIC or LD_KERNEL_FUSED", false;
     if (!(p->tau_f > 0.5)) return *why = "tau_f must exceed 1/2", false;
     if (!(p->rho0 > 0.0)) return *why = "rho0 must be positive", false;
     if (!isfinite(p->A0) || !isfinite(p->gamma) || !isfinite(p->kappa) || !isfinite(p->Gamma) || !isfinite(p->xi))
@@ -44,6 +46,10 @@ bool opt_dev(const void* p) { return p == nullptr || ld::is_device_pointer(p); }
 
 }  // namespace
 
+namespace lc {
+bool fused_supported(int nx, int ny, int nz) { return nx % 32 == 0 && ny % 8 == 0 && nz >= 3; }
+}  // namespace lc
+
 extern "C" {
 
 size_t lc_workspace_bytes(int nx, int ny, int nz, const lc_params* p) {
@@ -61,6 +67,9 @@ int lc_create(int nx, int ny, int nz, const lc_params* p, void* ws, size_t bytes
     if (!lc_params_ok(p, &why)) return ld::report_error(LD_EINVAL, "lc_create: %s", why);
     if (!ld::is_device_pointer(ws)) return ld::report_error(LD_EINVAL, "lc_create: workspace is not a device pointer");
     if ((uintptr_t)ws % kAlign) return ld::report_error(LD_EINVAL, "lc_create: workspace must be 256-byte aligned");
+    const bool fused_ok = lc::fused_supported(nx, ny, nz);
+    if (p->kernel == LD_KERNEL_FUSED && !fused_ok)
+        return ld::report_error(LD_EINVAL, "lc_create: LD_KERNEL_FUSED needs nx %% 32 == 0 and ny %% 8 == 0");
     size_t off[7];
     const size_t need = lc_layout(nx, ny, nz, p->precision, off);
     if (bytes < need)
@@ -82,6 +91,14 @@ int lc_create(int nx, int ny, int nz, const lc_params* p, void* ws, size_t bytes
     c->h = w + off[4];
     c->sigma = w + off[5];
     c->u = w + off[6];
+    c->kernel = p->kernel == LD_KERNEL_GENERIC ? LD_KERNEL_GENERIC
+              : p->kernel == LD_KERNEL_FUSED     ? LD_KERNEL_FUSED
+              : (fused_ok && p->precision == LD_FP32 ? LD_KERNEL_FUSED : LD_KERNEL_GENERIC);
+    int dev = 0, sms = 0;
+    c->num_sms = cudaGetDevice(&dev) == cudaSuccess &&
+                         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0
+                     ? sms
+                     : 152;
     c->cur = 0;
     c->initialized = false;
     c->stream = (cudaStream_t)cuda_stream;
@@ -93,6 +110,8 @@ int lc_destroy(lc_ctx* c) {
     free(c);
     return LD_OK;
 }
+
+int lc_step_kernel(const lc_ctx* c) { return c ? c->kernel : LD_EINVAL; }
 
 int lc_init(lc_ctx* c, const double* q, const double* rho, const double* u) {
     if (!c) return ld::report_error(LD_EINVAL, "lc_init: context is NULL");

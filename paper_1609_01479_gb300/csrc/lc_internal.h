@@ -17,6 +17,8 @@ struct lc_ctx {
     void* h;            // molecular field [5][npad]
     void* sigma;        // chemical stress [9][npad]
     void* u;            // velocity [3][npad]
+    int kernel;         // LD_KERNEL_GENERIC or LD_KERNEL_FUSED (resolved at create)
+    int num_sms;
     int cur;
     bool initialized;
     cudaStream_t stream;
@@ -29,6 +31,7 @@ namespace lc {
     cudaError_t step(lc_ctx* c);                                                              \
     cudaError_t out(lc_ctx* c, double* q, double* rho, double* u, double* h, double* f);     \
     }
+bool fused_supported(int nx, int ny, int nz);
 LC_PRECISION_LAUNCHERS(f64)
 LC_PRECISION_LAUNCHERS(f32)
 #undef LC_PRECISION_LAUNCHERS

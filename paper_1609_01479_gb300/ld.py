@@ -50,7 +50,7 @@ class LdParams(ctypes.Structure):
 class LcParams(ctypes.Structure):
     _fields_ = [("A0", ctypes.c_double), ("gamma", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("Gamma", ctypes.c_double), ("xi", ctypes.c_double), ("tau_f", ctypes.c_double),
-                ("rho0", ctypes.c_double), ("precision", ctypes.c_int)]
+                ("rho0", ctypes.c_double), ("precision", ctypes.c_int), ("kernel", ctypes.c_int)]
 
 
 class LdError(RuntimeError):
@@ -104,6 +104,7 @@ _SIGNATURES = {
                                  ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
     "lc_init": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "lc_step": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "lc_step_kernel": (ctypes.c_int, [_VP]),
     "lc_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "lc_destroy": (ctypes.c_int, [_VP]),
     "ld_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -371,9 +372,10 @@ def _lc_call(name, *args):
 
 
 def make_lc_params(A0=0.01, gamma=3.0, kappa=0.01, Gamma=0.3, xi=0.7, tau_f=1.0, rho0=1.0,
-                   precision="fp32") -> LcParams:
+                   precision="fp32", kernel="auto") -> LcParams:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    return LcParams(A0, gamma, kappa, Gamma, xi, tau_f, rho0, prec)
+    kern = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    return LcParams(A0, gamma, kappa, Gamma, xi, tau_f, rho0, prec, kern)
 
 
 def lc_workspace_bytes(nx, ny, nz, params: LcParams) -> int:
@@ -394,6 +396,12 @@ def lc_init(ctx, q, rho=None, u=None):
 
 def lc_step(ctx, nsteps: int):
     return _lc_call("lc_step", ctx, int(nsteps))
+
+
+def lc_step_kernel(ctx) -> str:
+    """The step kernel of a liquid-crystal context: "generic" or "fused"."""
+    k = int(lib().lc_step_kernel(ctx))
+    return {v: n for n, v in KERNELS.items()}[k]
 
 
 def lc_fields(ctx, q=None, rho=None, u=None, h=None, f=None):
@@ -438,6 +446,10 @@ class LcSim:
 
     def step(self, nsteps=1):
         lc_step(self.ctx, nsteps)
+
+    @property
+    def kernel(self) -> str:
+        return lc_step_kernel(self.ctx)
 
     def fields(self):
         mk = lambda *lead: torch.empty(*lead, *self.shape, dtype=torch.float64, device=self.device)  # noqa: E731

@@ -150,3 +150,7 @@ def test_lc_workspace_bytes_validates_its_arguments(ld):
     assert ws(2, 8, 8, p) == 0
     assert ws(8, 8, 8, ld.make_lc_params(precision="fp16dev")) == 0
     assert ws(8, 8, 8, ld.make_lc_params(tau_f=0.5)) == 0
+    # step kernels: auto, generic and fused only
+    assert ws(8, 8, 8, ld.make_lc_params(kernel="fused")) == b
+    assert ws(8, 8, 8, ld.make_lc_params(kernel="fused_staged")) == 0
+    assert ws(8, 8, 8, ld.make_lc_params(kernel=7)) == 0

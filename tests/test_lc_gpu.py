@@ -6,6 +6,10 @@ oracle, on ragged lattices and from a start with flow, density variations and
 nematic order far from equilibrium (every term of H, the stress, the
 co-rotation and the upwind advection is active). FP32: within 1e-5 after 50
 steps (FP32 rounding, 2^-24 per operation, accumulated over the steps).
+Both step kernels: the three per-site launches (any lattice) and the fused
+z-marching launch + Q update (nx % 32 == 0, ny % 8 == 0), which in FP64 gives
+the same bits as the per-site launches (the same operations in the same
+order), over several z-chunks and periodic wraps of every tile.
 Invariants: total mass and momentum conserved (the force is the divergence
 of a stress); a uniform bulk equilibrium Q = q0 (n n - I/3), at rest, is a
 fixed point.
@@ -47,9 +51,11 @@ def start(shape, seed):
     return q, rho, u
 
 
-def gpu_run(ld, shape, q, rho, u, steps, precision):
+def gpu_run(ld, shape, q, rho, u, steps, precision, kernel="auto", expect=None):
     nz, ny, nx = shape
-    sim = ld.LcSim(nx, ny, nz, precision=precision, **MODEL)
+    sim = ld.LcSim(nx, ny, nz, precision=precision, kernel=kernel, **MODEL)
+    if expect is not None:
+        assert sim.kernel == expect
     sim.init(torch.from_numpy(q), torch.from_numpy(rho), torch.from_numpy(u))
     sim.step(steps)
     out = {k: v.cpu().numpy() for k, v in sim.fields().items()}
@@ -74,17 +80,63 @@ def test_fp64_matches_the_oracle(ld, shape):
         assert rel(g[k], r[k]) <= 1e-12, (k, rel(g[k], r[k]))
 
 
-def test_fp32_within_its_rounding(ld):
+# (nz, ny, nx): one tile in x and y (the halo wraps onto the tile itself),
+# several tiles, and an nz the z-chunks divide unevenly into.
+@pytest.mark.parametrize("shape", [(3, 8, 32), (6, 16, 64), (9, 24, 32)])
+def test_fused_fp64_matches_the_oracle(ld, shape):
+    q, rho, u = start(shape, seed=7 + sum(shape))
+    g = gpu_run(ld, shape, q, rho, u, 10, "fp64", kernel="fused", expect="fused")
+    r = oracle_run(shape, q, rho, u, 10)
+    for k in ("q", "f", "rho", "u"):
+        assert rel(g[k], r[k]) <= 1e-12, (k, rel(g[k], r[k]))
+
+
+# 64 x 64 x 128: 32 tile columns, so the fused launch marches 16 planes per
+# CTA (the small lattices above take one) and its rings turn over.
+@pytest.mark.parametrize("shape", [(12, 16, 64), (64, 64, 128)])
+def test_fused_fp64_is_bitwise_the_per_site_step(ld, shape):
+    q, rho, u = start(shape, seed=21)
+    a = gpu_run(ld, shape, q, rho, u, 5, "fp64", kernel="fused", expect="fused")
+    b = gpu_run(ld, shape, q, rho, u, 5, "fp64", kernel="generic", expect="generic")
+    for k in ("q", "f", "rho", "u", "h"):
+        assert np.array_equal(a[k], b[k]), k
+    if shape[0] == 64:
+        r = oracle_run(shape, q, rho, u, 5)
+        for k in ("q", "f", "rho", "u"):
+            assert rel(a[k], r[k]) <= 1e-12, (k, rel(a[k], r[k]))
+
+
+def test_fused_fp32_tracks_the_per_site_step(ld):
+    """FP32 over 16-plane chunks (128 x 64 x 128): the two kernels round the
+    same operations, up to the compiler's FMA contraction in each."""
+    shape = (128, 64, 128)
+    q, rho, u = start(shape, seed=5)
+    a = gpu_run(ld, shape, q, rho, u, 20, "fp32", kernel="fused", expect="fused")
+    b = gpu_run(ld, shape, q, rho, u, 20, "fp32", kernel="generic", expect="generic")
+    for k in ("q", "f", "rho"):
+        assert rel(a[k], b[k]) <= 1e-6, (k, rel(a[k], b[k]))
+
+
+def test_kernel_choice(ld):
+    assert ld.LcSim(32, 8, 4, precision="fp32").kernel == "fused"
+    assert ld.LcSim(32, 8, 4, precision="fp64").kernel == "generic"
+    assert ld.LcSim(30, 8, 4, precision="fp32").kernel == "generic"
+    with pytest.raises(ld.LdError):
+        ld.LcSim(30, 8, 4, precision="fp32", kernel="fused")
+
+
+@pytest.mark.parametrize("kernel", ["fused", "generic"])
+def test_fp32_within_its_rounding(ld, kernel):
     shape = (16, 16, 32)
     q, rho, u = start(shape, seed=3)
-    g = gpu_run(ld, shape, q, rho, u, 50, "fp32")
+    g = gpu_run(ld, shape, q, rho, u, 50, "fp32", kernel=kernel, expect=kernel)
     r = oracle_run(shape, q, rho, u, 50)
     for k in ("q", "f", "rho"):
         assert rel(g[k], r[k]) <= 1e-5, (k, rel(g[k], r[k]))
 
 
-def test_mass_and_momentum_are_conserved(ld):
-    shape = (8, 12, 16)
+@pytest.mark.parametrize("shape", [(8, 12, 16), (8, 8, 32)])
+def test_mass_and_momentum_are_conserved(ld, shape):
     q, rho, u = start(shape, seed=9)
     c, _ = oracle.lattice()
 
@@ -93,7 +145,8 @@ def test_mass_and_momentum_are_conserved(ld):
 
     f0 = oracle.lc_init(shape, oracle.lc_param_vector(**MODEL), rho=rho, u=u)
     m0, p0 = totals(f0)
-    g = gpu_run(ld, shape, q, rho, u, 100, "fp64")
+    kernel = "fused" if shape[2] % 32 == 0 and shape[1] % 8 == 0 else "generic"
+    g = gpu_run(ld, shape, q, rho, u, 100, "fp64", kernel=kernel, expect=kernel)
     m1, p1 = totals(g["f"])
     assert abs(m1 - m0) < 1e-11 * f0.size
     assert np.abs(p1 - p0).max() < 1e-12 * f0.size
