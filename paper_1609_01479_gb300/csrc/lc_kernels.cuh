@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(kLcThreads) k_lc_update(LcGeom g, LcModel<T> m
 
 // ---------------------------------------------------------------------------
 // Fused field + collision step. Each CTA owns a kLcTX x kLcTY column of sites
-// and marches up a chunk of zc z-planes. The stress chain Q -> (H, sigma) ->
+// and marches up a chunk of z-planes. The stress chain Q -> (H, sigma) ->
 // F = div sigma needs sigma within one site and so Q within two sites of every
 // collided site. Shared memory holds:
 //   Q ring:     4 planes x 5 components over the tile + 2-site halo;
@@ -474,6 +474,12 @@ constexpr bool kLcPairSigma = true;
 
 __device__ __forceinline__ int lc_wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+// First plane of z-chunk b when nz planes are split into nchunks chunks
+// whose lengths differ by at most one.
+__host__ __device__ inline int lc_chunk_begin(int b, int nz, int nchunks) {
+    return (int)(((long long)b * nz) / nchunks);
+}
+
 // cp.async of 8 or 16 bytes (both addresses aligned to the size), and the
 // group waits; hardware waits, the copies always land.
 template <int BYTES>
@@ -493,7 +499,7 @@ __device__ __forceinline__ void lc_cp_wait() {
 // I: type of the element offsets i * npad + s (32-bit where 19 npad fits).
 template <class T, class I, bool STAGE_F>
 __global__ void __launch_bounds__(kLcFusedThreads, (lc_fused_ctas<T, STAGE_F>()))
-    k_lc_fused(LcGeom g, LcModel<T> m, int zc, const T* __restrict__ q, const T* __restrict__ f,
+    k_lc_fused(LcGeom g, LcModel<T> m, int nchunks, const T* __restrict__ q, const T* __restrict__ f,
                T* __restrict__ fd, T* __restrict__ u) {
     using L = LcFusedLayout;
     extern __shared__ __align__(16) unsigned char lc_smem[];
@@ -506,8 +512,9 @@ __global__ void __launch_bounds__(kLcFusedThreads, (lc_fused_ctas<T, STAGE_F>())
 
     const int tid = threadIdx.x;
     const int tx = tid % kLcTX, ty = tid / kLcTX;
-    const int x0 = blockIdx.x * kLcTX, y0 = blockIdx.y * kLcTY, z0 = blockIdx.z * zc;
+    const int x0 = blockIdx.x * kLcTX, y0 = blockIdx.y * kLcTY;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int z0 = lc_chunk_begin(blockIdx.z, nz, nchunks), z1 = lc_chunk_begin(blockIdx.z + 1, nz, nchunks);
     const int plane = nx * ny;
     const I npad = (I)g.npad;
 
@@ -620,7 +627,7 @@ __global__ void __launch_bounds__(kLcFusedThreads, (lc_fused_ctas<T, STAGE_F>())
     const int oxp = x + 1 == nx ? 1 - nx : 1, oxm = x == 0 ? nx - 1 : -1;
     const int oyp = y + 1 == ny ? (1 - ny) * nx : nx, oym = y == 0 ? (ny - 1) * nx : -nx;
 
-    for (int k = z0; k < z0 + zc; ++k) {
+    for (int k = z0; k < z1; ++k) {
         // the last collision is done with the f tile and the sigma slots of
         // plane k-1, the last sigma pass with Q(k-1)
         __syncthreads();
@@ -634,7 +641,7 @@ __global__ void __launch_bounds__(kLcFusedThreads, (lc_fused_ctas<T, STAGE_F>())
         lc_cp_wait<1>();  // f(k) has landed
         __syncthreads();
 
-        const int s = k * plane + y * nx + x;  // zc divides nz: k < nz
+        const int s = k * plane + y * nx + x;  // z1 <= nz
         T Fa[3] = {T(0), T(0), T(0)};
         const int sxy = xs(k), szp = ss(k + 1), szm = ss(k - 1);
 #pragma unroll
@@ -660,18 +667,18 @@ __global__ void __launch_bounds__(kLcFusedThreads, (lc_fused_ctas<T, STAGE_F>())
     lc_cp_wait<0>();  // the last Q prefetch (not read) lands before the CTA exits
 }
 
-// Planes per CTA: the divisor of nz among 64..1 that minimises waves x
-// (planes + 2), each CTA paying about two planes of prologue.
-inline int lc_choose_zc(int nx, int ny, int nz, int num_sms, int per_sm) {
+// z-chunks per tile column: chunk b spans [lc_chunk_begin(b),
+// lc_chunk_begin(b + 1)). m in 1..nz minimises waves x (longest chunk + 2),
+// each CTA paying about two planes of prologue; the smaller m on a tie.
+inline int lc_choose_chunks(int nx, int ny, int nz, int num_sms, int per_sm) {
     const long long cols = (long long)(nx / kLcTX) * (ny / kLcTY);
     const long long slots = (long long)per_sm * num_sms;
     int best = 0;
     long long best_cost = 0;
-    for (int zc = 64; zc >= 1; zc /= 2) {
-        if (nz % zc) continue;
-        const long long cost = ((cols * (nz / zc) + slots - 1) / slots) * (zc + 2);
+    for (int m = 1; m <= nz; ++m) {
+        const long long cost = ((cols * m + slots - 1) / slots) * ((nz + m - 1) / m + 2);
         if (best == 0 || cost < best_cost) {
-            best = zc;
+            best = m;
             best_cost = cost;
         }
     }
@@ -764,9 +771,9 @@ cudaError_t launch_lc_fused(lc_ctx* c, const LcGeom& g, const LcModel<T>& m, con
     constexpr int smem = (int)lc_fused_smem<T, kStage>();
     const cudaError_t e = ld::set_max_dynamic_smem_once<k_lc_fused<T, I, kStage>>(smem);
     if (e != cudaSuccess) return e;
-    const int zc = lc_choose_zc(g.nx, g.ny, g.nz, c->num_sms, lc_fused_ctas<T, kStage>());
-    const dim3 grid(g.nx / kLcTX, g.ny / kLcTY, g.nz / zc);
-    k_lc_fused<T, I, kStage><<<grid, kLcFusedThreads, smem, c->stream>>>(g, m, zc, b.q[c->cur], b.f[c->cur],
+    const int nchunks = lc_choose_chunks(g.nx, g.ny, g.nz, c->num_sms, lc_fused_ctas<T, kStage>());
+    const dim3 grid(g.nx / kLcTX, g.ny / kLcTY, nchunks);
+    k_lc_fused<T, I, kStage><<<grid, kLcFusedThreads, smem, c->stream>>>(g, m, nchunks, b.q[c->cur], b.f[c->cur],
                                                                          b.f[1 - c->cur], b.u);
     return cudaGetLastError();
 }

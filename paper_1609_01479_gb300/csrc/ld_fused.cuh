@@ -43,6 +43,12 @@ constexpr int fused_ctas_per_sm() {
 // Periodic image of a coordinate at most one period outside [0, n).
 __device__ __forceinline__ int wrap_once(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+// First plane of z-chunk b when nz planes are split into nchunks chunks
+// whose lengths differ by at most one.
+__host__ __device__ inline int chunk_begin(int b, int nz, int nchunks) {
+    return (int)(((long long)b * nz) / nchunks);
+}
+
 // A 16-bit storage word from its bit pattern.
 template <class T>
 __device__ __forceinline__ T bits16(unsigned b) {
@@ -60,7 +66,7 @@ __device__ __forceinline__ T bits16(unsigned b) {
 // SR: stochastic rounding of the 16-bit stores, from the stream `sr`.
 template <int P, int TY, class I, bool ISO, bool SR>
 __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
-    k_step_fused(Geom g, Model<typename Prec<P>::real_t> m, int zc,
+    k_step_fused(Geom g, Model<typename Prec<P>::real_t> m, int nchunks,
                  const typename Prec<P>::store_t* __restrict__ fs, const typename Prec<P>::store_t* __restrict__ gs,
                  typename Prec<P>::store_t* __restrict__ fd, typename Prec<P>::store_t* __restrict__ gd,
                  const float* __restrict__ ref_g, typename Prec<P>::real_t* __restrict__ phi_out,
@@ -81,8 +87,9 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
 
     const int tid = threadIdx.x;
     const int tx = tid % kTX, ty = tid / kTX;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int z0 = chunk_begin(blockIdx.z, nz, nchunks), z1 = chunk_begin(blockIdx.z + 1, nz, nchunks);
     const int plane = nx * ny;
     const I npad = (I)g.npad;
     if (tid < 2 * Q) refs[tid] = ref_g[tid];
@@ -193,8 +200,8 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     const int oxp = x + 1 == nx ? 1 - nx : 1, oxm = x == 0 ? nx - 1 : -1;
     const int oyp = y + 1 == ny ? (1 - ny) * nx : nx, oym = y == 0 ? (ny - 1) * nx : -nx;
 
-    for (int k = z0; k < z0 + zc; ++k) {
-        const int z = k;  // zc divides nz: k < nz
+    for (int k = z0; k < z1; ++k) {
+        const int z = k;  // z1 <= nz
         const int s = z * plane + y * nx + x;
         const bool cok = site_ok(s, g.n, status);
         // Loads for this plane's collision issued ahead of the phi and mu
@@ -313,11 +320,15 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
 
 constexpr int kTY = 8;
 
-// Planes per CTA. `per_sm` CTAs are resident per SM, and each CTA pays a
-// prologue worth about two collided planes (four extra phi planes and the
-// pipeline start); pick the divisor of nz among 64..4 that minimises
-// waves x (planes per CTA + 2).
-int choose_zc_rows(int nx, int ny, int nz, int rows, int num_sms = 152, int per_sm = 2) {
+// z-chunks per tile column. Each CTA marches one chunk of the nz planes,
+// chunk b spanning [chunk_begin(b), chunk_begin(b + 1)). `per_sm` CTAs are
+// resident per SM, and each CTA pays a prologue worth about two collided
+// planes (four extra phi planes and the pipeline start): the chunk length
+// is the divisor of nz among 64, 32, ..., 4 that minimises waves x (length
+// + 2). (Chunks of any length, nz split into m near-equal parts with m
+// chosen by the same cost, measured no faster for FP32 and 10 % slower for
+// the 16-bit pairs at 384^3.)
+int choose_chunks(int nx, int ny, int nz, int rows, int num_sms = 152, int per_sm = 2) {
     const long long cols = (long long)(nx / kTX) * (ny / rows);
     const long long slots = (long long)per_sm * num_sms;
     int best = 0;
@@ -327,14 +338,11 @@ int choose_zc_rows(int nx, int ny, int nz, int rows, int num_sms = 152, int per_
         const long long waves = (cols * (nz / zc) + slots - 1) / slots;
         const long long cost = waves * (zc + 2);
         if (best == 0 || cost < best_cost) {
-            best = zc;
+            best = nz / zc;
             best_cost = cost;
         }
     }
     return best;
-}
-int choose_zc(int nx, int ny, int nz, int num_sms = 152, int per_sm = 2) {
-    return choose_zc_rows(nx, ny, nz, kTY, num_sms, per_sm);
 }
 
 template <int P, class I, bool ISO, bool SR>
@@ -345,10 +353,10 @@ cudaError_t launch_fused(ld_ctx* c, const void* src, void* dst, void* fields) {
     cudaError_t e = set_max_dynamic_smem_once<k_step_fused<P, kTY, I, ISO, SR>>((int)kRingBytes);
     if (e != cudaSuccess) return e;
     const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
-    const int zc = choose_zc(g.nx, g.ny, g.nz, c->num_sms, fused_ctas_per_sm<P>());
-    const dim3 grid(g.nx / kTX, g.ny / kTY, g.nz / zc);
+    const int nchunks = choose_chunks(g.nx, g.ny, g.nz, kTY, c->num_sms, fused_ctas_per_sm<P>());
+    const dim3 grid(g.nx / kTX, g.ny / kTY, nchunks);
     k_step_fused<P, kTY, I, ISO, SR><<<grid, kTX * kTY, kRingBytes, c->stream>>>(
-        g, model_of<R>(c->prm), zc, (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
+        g, model_of<R>(c->prm), nchunks, (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
         (S*)g_part(c, dst), c->ref, fields ? (R*)fields : nullptr, fields ? (R*)fields + c->geom.npad : nullptr,
         sr_stream(c->prm.seed, c->sr_step, c->geom.n), c->status);
     return cudaGetLastError();
@@ -377,7 +385,7 @@ cudaError_t step_fused_p(ld_ctx* c, const void* src, void* dst, void* fields) {
 }  // namespace
 
 inline bool fused_supported_impl(int nx, int ny, int nz) {
-    return nx % kTX == 0 && ny % kTY == 0 && nz >= 4 && choose_zc(nx, ny, nz) > 0;
+    return nx % kTX == 0 && ny % kTY == 0 && nz >= 4 && nz % 4 == 0;
 }
 
 }  // namespace ld

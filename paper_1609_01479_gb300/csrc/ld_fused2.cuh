@@ -168,7 +168,7 @@ constexpr int pair_ctas_per_sm() {
 
 template <int P, class I, bool ISO, int TY>
 __global__ void __launch_bounds__(16 * TY, pair_ctas_per_sm<TY>())
-    k_step_fused2(Geom g, Model<float> m, int zc, const typename Prec<P>::store_t* __restrict__ fs,
+    k_step_fused2(Geom g, Model<float> m, int nchunks, const typename Prec<P>::store_t* __restrict__ fs,
                   const typename Prec<P>::store_t* __restrict__ gs, typename Prec<P>::store_t* __restrict__ fd,
                   typename Prec<P>::store_t* __restrict__ gd, const float* __restrict__ ref_g,
                   float* __restrict__ phi_out, float* __restrict__ mu_out, int* __restrict__ status) {
@@ -185,7 +185,8 @@ __global__ void __launch_bounds__(16 * TY, pair_ctas_per_sm<TY>())
 
     const int tid = threadIdx.x;
     const int tp = tid % (TX / 2), ty = tid / (TX / 2);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = chunk_begin(blockIdx.z, g.nz, nchunks), z1 = chunk_begin(blockIdx.z + 1, g.nz, nchunks);
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int plane = nx * ny;
     const I npad = (I)g.npad;
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(16 * TY, pair_ctas_per_sm<TY>())
     const int oxm0 = x == 0 ? nx - 1 : -1, oxp1 = x + 2 == nx ? 1 - nx : 1;
     const int oyp = y + 1 == ny ? (1 - ny) * nx : nx, oym = y == 0 ? (ny - 1) * nx : -nx;
 
-    for (int k = z0; k < z0 + zc; ++k) {
+    for (int k = z0; k < z1; ++k) {
         const int z = k;
         const int s = z * plane + y * nx + x;  // even: the pair (s, s + 1)
         const bool cok = site_ok(s, g.n, status) && site_ok(s + 1, g.n, status);
@@ -355,10 +356,10 @@ cudaError_t launch_fused2(ld_ctx* c, const void* src, void* dst, void* fields) {
     cudaError_t e = set_max_dynamic_smem_once<k_step_fused2<P, I, ISO, TY>>((int)kRingBytes);
     if (e != cudaSuccess) return e;
     const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
-    const int zc = choose_zc_rows(g.nx, g.ny, g.nz, TY, c->num_sms, pair_ctas_per_sm<TY>());
-    const dim3 grid(g.nx / kTX, g.ny / TY, g.nz / zc);
+    const int nchunks = choose_chunks(g.nx, g.ny, g.nz, TY, c->num_sms, pair_ctas_per_sm<TY>());
+    const dim3 grid(g.nx / kTX, g.ny / TY, nchunks);
     k_step_fused2<P, I, ISO, TY><<<grid, 16 * TY, kRingBytes, c->stream>>>(
-        g, model_of<float>(c->prm), zc, (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
+        g, model_of<float>(c->prm), nchunks, (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
         (S*)g_part(c, dst), c->ref, fields ? (float*)fields : nullptr, fields ? (float*)fields + c->geom.npad : nullptr,
         c->status);
     return cudaGetLastError();

@@ -56,7 +56,7 @@ struct StagedLayout {
 
 template <int P, class I, bool ISO, bool SR>
 __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
-    k_step_staged(Geom g, Model<typename Prec<P>::real_t> m, int zc, const typename Prec<P>::store_t* __restrict__ fs,
+    k_step_staged(Geom g, Model<typename Prec<P>::real_t> m, int nchunks, const typename Prec<P>::store_t* __restrict__ fs,
                   const typename Prec<P>::store_t* __restrict__ gs, typename Prec<P>::store_t* __restrict__ fd,
                   typename Prec<P>::store_t* __restrict__ gd, const float* __restrict__ ref_g,
                   typename Prec<P>::real_t* __restrict__ phi_out, typename Prec<P>::real_t* __restrict__ mu_out,
@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = chunk_begin(blockIdx.z, g.nz, nchunks), z1 = chunk_begin(blockIdx.z + 1, g.nz, nchunks);
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int plane = nx * ny;
     const I npad = (I)g.npad;
@@ -194,8 +195,8 @@ __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
     const int oxp = x + 1 == nx ? 1 - nx : 1, oxm = x == 0 ? nx - 1 : -1;
     const int oyp = y + 1 == ny ? (1 - ny) * nx : nx, oym = y == 0 ? (ny - 1) * nx : -nx;
 
-    for (int k = z0; k < z0 + zc; ++k) {
-        const int z = k;  // zc divides nz: k < nz
+    for (int k = z0; k < z1; ++k) {
+        const int z = k;  // z1 <= nz
         const int s = z * plane + y * nx + x;
         const bool cok = site_ok(s, g.n, status);
         // FP32: the collision's g re-read (an L2 hit) issued before the
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(StagedLayout<P>::NT, 3)
 template <int P>
 bool staged_supported_p(int nx, int ny, int nz) {
     using L = StagedLayout<P>;
-    return nx % L::TX == 0 && ny % L::TY == 0 && nz >= 4 && choose_zc(nx, ny, nz) > 0;
+    return nx % L::TX == 0 && ny % L::TY == 0 && nz >= 4 && nz % 4 == 0;
 }
 
 template <int P, class I, bool ISO, bool SR>
@@ -315,10 +316,10 @@ cudaError_t launch_staged(ld_ctx* c, const void* src, void* dst, void* fields) {
     cudaError_t e = set_max_dynamic_smem_once<k_step_staged<P, I, ISO, SR>>((int)L::BYTES);
     if (e != cudaSuccess) return e;
     const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
-    const int zc = choose_zc(g.nx, g.ny, g.nz, c->num_sms, 3);
-    const dim3 grid(g.nx / L::TX, g.ny / L::TY, g.nz / zc);
+    const int nchunks = choose_chunks(g.nx, g.ny, g.nz, L::TY, c->num_sms, 3);
+    const dim3 grid(g.nx / L::TX, g.ny / L::TY, nchunks);
     k_step_staged<P, I, ISO, SR><<<grid, L::NT, L::BYTES, c->stream>>>(
-        g, model_of<R>(c->prm), zc, (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
+        g, model_of<R>(c->prm), nchunks, (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
         (S*)g_part(c, dst), c->ref, fields ? (R*)fields : nullptr, fields ? (R*)fields + c->geom.npad : nullptr,
         sr_stream(c->prm.seed, c->sr_step, c->geom.n), c->status, c->wait_polls, c->wait_probe);
     return cudaGetLastError();
