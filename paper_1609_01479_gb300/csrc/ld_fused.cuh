@@ -33,6 +33,15 @@ namespace {
 
 constexpr int kTX = 32;
 
+// FP32: where the collision's loads of the plane are issued. Before the phi
+// pass (kF32TopLoad) or after it (kF32MidLoad): 0 neither, 1 the g re-read (an
+// L2 hit), 2 f (from HBM); the rest at the collision. Measured on one box at
+// 256^3 / 384^3 (fraction of HBM): g after the phi pass 0.718 / 0.734, g
+// before it 0.717 / 0.715, f after it (g before) 0.697 / 0.697, f before and
+// g after 0.658 / 0.665, f after and g at the collision 0.677 / 0.684, f
+// before 0.697 / 0.666.
+constexpr int kF32TopLoad = 0, kF32MidLoad = 1;
+
 // Resident CTAs per SM the kernel is compiled for: three 256-thread CTAs
 // (80 registers a thread) with FP32 arithmetic, two with FP64.
 template <int P>
@@ -77,7 +86,12 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
     constexpr int MW = kTX + 2, MH = TY + 2;  // mu ring plane
     constexpr int NT = kTX * TY;
     constexpr bool kKeepG = sizeof(S) == 2;
-    constexpr bool kEarlyG = sizeof(S) == 4;  // FP64 has no registers to spare for it
+    // Where the collision's loads are issued (FP64 has no registers to spare
+    // for either): before the phi pass (top) or after it (mid).
+    constexpr bool k32 = sizeof(S) == 4;
+    constexpr bool kTopG = k32 && kF32TopLoad == 1, kTopF = k32 && kF32TopLoad == 2;
+    constexpr bool kMidG = k32 && kF32MidLoad == 1, kMidF = kKeepG || (k32 && kF32MidLoad == 2);
+    constexpr bool kEarlyG = kTopG || kMidG, kEarlyF = kTopF || kMidF;
     __shared__ R phis[3][PH][PW];
     __shared__ R mus[3][MH][MW];
     __shared__ float refs[2 * Q];
@@ -204,22 +218,25 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
         const int z = k;  // z1 <= nz
         const int s = z * plane + y * nx + x;
         const bool cok = site_ok(s, g.n, status);
-        // Loads for this plane's collision issued ahead of the phi and mu
-        // passes, so that their latency overlaps that work: in FP32 the g
-        // re-read (an L2 hit), in the 16-bit forms (g kept in shared memory)
-        // f, after the phi pass's own loads. Issuing f early in FP32
-        // measured slower.
+        // Loads for this plane's collision issued ahead of the mu pass, after
+        // the phi pass's own loads, so that their latency overlaps that work:
+        // in FP32 the g re-read (an L2 hit), in the 16-bit forms (g kept in
+        // shared memory) f. Other placements measured slower (kF32TopLoad).
         S gpre[Q], fpre[Q];
-        if constexpr (kEarlyG) {
+        auto load_g = [&]() {
 #pragma unroll
             for (int i = 0; i < Q; ++i) gpre[i] = cok ? ld_l2_hint_now(gs + i * npad + s, drop_l2) : S(0);
-        }
-        __syncthreads();  // previous collision done with phi(k-1) and mu(k-2) slots
-        phi_plane(k + 2, ps(k + 2));
-        if constexpr (kKeepG) {
+        };
+        auto load_f = [&]() {
 #pragma unroll
             for (int i = 0; i < Q; ++i) fpre[i] = cok ? ld_l2_hint_now(fs + i * npad + s, drop_l2) : S(0);
-        }
+        };
+        if constexpr (kTopG) load_g();
+        if constexpr (kTopF) load_f();
+        __syncthreads();  // previous collision done with phi(k-1) and mu(k-2) slots
+        phi_plane(k + 2, ps(k + 2));
+        if constexpr (kMidF) load_f();
+        if constexpr (kMidG) load_g();
         __syncthreads();
         mu_plane(ms(k + 1), ps(k), ps(k + 1), ps(k + 2));
         __syncthreads();
@@ -272,7 +289,7 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
             R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                f[i] = Prec<P>::decode(cok ? fs[i * npad + s] : S(0), refs[i]);
+                f[i] = Prec<P>::decode(kEarlyF ? fpre[i] : (cok ? fs[i * npad + s] : S(0)), refs[i]);
                 rho += f[i];
                 add_c(i, f[i], jx, jy, jz);
             }

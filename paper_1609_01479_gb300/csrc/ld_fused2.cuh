@@ -161,6 +161,10 @@ __device__ __forceinline__ unsigned pack2(float2 a) {
 
 // CTAs of 16 x TY threads (16 pairs x TY rows of a 32 x TY tile); resident
 // CTAs per SM chosen so that a thread has 128 registers (fewer spill).
+// Issue the plane's f loads before the psi pass (true) or after its own loads
+// (false), to be used after the mu pass.
+constexpr bool kPairFBeforePhi = false;
+
 template <int TY>
 constexpr int pair_ctas_per_sm() {
     return TY == 8 ? 4 : 2;
@@ -263,11 +267,15 @@ __global__ void __launch_bounds__(16 * TY, pair_ctas_per_sm<TY>())
         const int z = k;
         const int s = z * plane + y * nx + x;  // even: the pair (s, s + 1)
         const bool cok = site_ok(s, g.n, status) && site_ok(s + 1, g.n, status);
+        unsigned fpre[Q];  // issued before or after the psi pass's own loads, used after the mu pass
+        auto load_f = [&]() {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) fpre[i] = cok ? ld_l2_hint_pair_now(fs + i * npad + s, drop_l2) : 0u;
+        };
+        if constexpr (kPairFBeforePhi) load_f();
         __syncthreads();  // previous collision done with psi(k-1) and mu(k-2) slots
         phi_plane(k + 2, ps(k + 2));
-        unsigned fpre[Q];  // issued after the psi pass's own loads, used after the mu pass
-#pragma unroll
-        for (int i = 0; i < Q; ++i) fpre[i] = cok ? ld_l2_hint_pair_now(fs + i * npad + s, drop_l2) : 0u;
+        if constexpr (!kPairFBeforePhi) load_f();
         __syncthreads();
         mu_plane(ms(k + 1), ps(k), ps(k + 1), ps(k + 2));
         __syncthreads();
