@@ -338,13 +338,19 @@ __global__ void __launch_bounds__(kTX * TY, fused_ctas_per_sm<P>())
 constexpr int kTY = 8;
 
 // z-chunks per tile column. Each CTA marches one chunk of the nz planes,
-// chunk b spanning [chunk_begin(b), chunk_begin(b + 1)). `per_sm` CTAs are
-// resident per SM, and each CTA pays a prologue worth about two collided
-// planes (four extra phi planes and the pipeline start): the chunk length
-// is the divisor of nz among 64, 32, ..., 4 that minimises waves x (length
-// + 2). (Chunks of any length, nz split into m near-equal parts with m
-// chosen by the same cost, measured no faster for FP32 and 10 % slower for
-// the 16-bit pairs at 384^3.)
+// chunk b spanning [chunk_begin(b), chunk_begin(b + 1)). The chunk length zc
+// is the divisor of nz among 64, 32, ..., 4 that minimises
+//   (zc + 4) x (columns x m / (per_sm x SMs) + 0.6),   m = nz / zc:
+// each CTA pays a prologue of about four planes (four extra phi planes, two
+// mu planes and the pipeline start), the m chunks of every column are spread
+// over the resident CTA slots, and the tail of the launch costs about 0.6 of
+// one chunk (CTAs are scheduled as slots free up, so less than a whole
+// wave). The weights reproduce the measured order of the lengths (fraction of
+// measured HBM): 256^3 FP32 32 (0.728) > 16 (0.718) > 8 (0.706) > 64 (0.666);
+// 256^3 16-bit pairs 16 (0.545) ~ 32 (0.542) > 64 (0.519) ~ 8 (0.514); 384^3
+// FP32 64 ahead of 32 and 16 (16.4 k against 15.5-15.8 k MLUPS). Chunks of
+// any length (nz split into m near-equal parts) measured no faster for FP32
+// and 10 % slower for the 16-bit pairs at 384^3.
 int choose_chunks(int nx, int ny, int nz, int rows, int num_sms = 152, int per_sm = 2) {
     const long long cols = (long long)(nx / kTX) * (ny / rows);
     const long long slots = (long long)per_sm * num_sms;
@@ -352,10 +358,10 @@ int choose_chunks(int nx, int ny, int nz, int rows, int num_sms = 152, int per_s
     long long best_cost = 0;
     for (int zc = 64; zc >= 4; zc /= 2) {
         if (nz % zc) continue;
-        const long long waves = (cols * (nz / zc) + slots - 1) / slots;
-        const long long cost = waves * (zc + 2);
+        const long long m = nz / zc;
+        const long long cost = (zc + 4) * (10 * cols * m + 6 * slots);  // x 10 slots
         if (best == 0 || cost < best_cost) {
-            best = nz / zc;
+            best = (int)m;
             best_cost = cost;
         }
     }
