@@ -81,6 +81,12 @@ __device__ __forceinline__ unsigned ld_l2_hint_pair(const void* p, uint64_t pol)
     asm("ld.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
     return v;
 }
+// Four 16-bit values (8 bytes, 8-byte aligned) with an L2 cache policy.
+__device__ __forceinline__ uint2 ld_l2_hint_quad(const void* p, uint64_t pol) {
+    uint2 v;
+    asm("ld.global.L2::cache_hint.v2.b32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
 // The same, issued where it is written (volatile), to overlap its latency.
 __device__ __forceinline__ unsigned ld_l2_hint_pair_now(const void* p, uint64_t pol) {
     unsigned v;

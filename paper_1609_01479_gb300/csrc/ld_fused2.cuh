@@ -164,6 +164,15 @@ __device__ __forceinline__ unsigned pack2(float2 a) {
 // Issue the plane's f loads before the psi pass (true) or after its own loads
 // (false), to be used after the mu pass.
 constexpr bool kPairFBeforePhi = false;
+// The psi pass on four-site quads (one round of 8-byte loads for 128 threads)
+// rather than pairs (two rounds of 4-byte loads), per storage form. Measured
+// at 384^3 / 256^3 (fraction of HBM): BF16-dev 0.593 / 0.578 with quads
+// against 0.568 / 0.539; FP16-dev 0.563 / 0.548 against 0.569 / 0.538 (its
+// quad kernel keeps a 12-byte spill at 128 registers).
+template <int P>
+__host__ __device__ constexpr bool phi_quads() {
+    return P == LD_BF16DEV;
+}
 
 template <int TY>
 constexpr int pair_ctas_per_sm() {
@@ -201,8 +210,42 @@ __global__ void __launch_bounds__(16 * TY, pair_ctas_per_sm<TY>())
     // psi of plane zp over the tile + 2-halo: two x-adjacent sites from one
     // 32-bit load per direction; the tile's own pairs also go to the g ring.
     auto phi_plane = [&](int zp, int slot) {
-        constexpr int PW2 = PW / 2;
         const int zoff = wrap_once(zp, nz) * plane;
+        if constexpr (phi_quads<P>()) {
+            // four x-adjacent sites from one 8-byte load per direction, over
+            // x0-4 .. x0+TX+3 (quads aligned to four sites; the outermost
+            // two sites on each side are loaded and not kept)
+            constexpr int QQ = (TX + 8) / 4;
+            for (int idx = tid; idx < QQ * PH; idx += NT) {
+                const int qx = 4 * (idx % QQ), hy = idx / QQ;
+                const int s = zoff + wrap_once(y0 + hy - 2, ny) * nx + wrap_once(x0 + qx - 4, nx);  // multiple of 4
+                const bool sok = site_ok(s, g.n, status) && site_ok(s + 3, g.n, status);
+                const bool interior = qx >= 4 && qx < TX + 4 && hy >= 2 && hy < TY + 2;
+                S* keep = gring + ((size_t)slot * Q * TY + (hy - 2)) * TX + (qx - 4);
+                float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const uint2 v = sok ? ld_l2_hint_quad(gs + i * npad + s, keep_l2) : make_uint2(0u, 0u);
+                    const unsigned short h[4] = {(unsigned short)(v.x & 0xffffu), (unsigned short)(v.x >> 16),
+                                                 (unsigned short)(v.y & 0xffffu), (unsigned short)(v.y >> 16)};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if constexpr (P == LD_FP16DEV)
+                            a[j] = add_f16(a[j], h[j]);
+                        else
+                            a[j] = add_bf16(a[j], h[j]);
+                    }
+                    if (interior) *reinterpret_cast<uint2*>(keep + i * (TY * TX)) = v;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int hx = qx - 2 + j;  // psi frame: x0-2 .. x0+TX+1
+                    if (hx >= 0 && hx < PW) phis[slot][hy][hx] = a[j];
+                }
+            }
+            return;
+        }
+        constexpr int PW2 = PW / 2;
         for (int idx = tid; idx < PW2 * PH; idx += NT) {
             const int hx = 2 * (idx % PW2), hy = idx / PW2;
             const int s = zoff + wrap_once(y0 + hy - 2, ny) * nx + wrap_once(x0 + hx - 2, nx);  // even
