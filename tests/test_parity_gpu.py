@@ -393,6 +393,25 @@ def test_staged_kernel_matches_oracle_and_generic(ld, precision, shape):
     assert rel_l2(b["f"], a["f"]) <= same
 
 
+@pytest.mark.parametrize("stencil", [7, 19])
+@pytest.mark.parametrize("shape", [(12, 32, 64), (8, 48, 32)])
+def test_fp32_fused_several_y_tiles(ld, shape, stencil):
+    """FP32 fused step over four and six y-tiles (the lowest tile's halo and
+    the highest one's wrapping periodically), both stencil pairs: the same
+    arithmetic as the staged kernel (1e-6, FMA contraction only) and within
+    the FP32 bound of the oracle."""
+    nz, ny, nx = shape
+    phi = inputs.spinodal_phi(nx, ny, nz, seed=23, amplitude=0.3)
+    prm = oracle.param_vector(stencil=stencil)
+    a = gpu_run(ld, phi, 20, precision="fp32", kernel="fused", prm=prm)
+    b = gpu_run(ld, phi, 20, precision="fp32", kernel="fused_staged", prm=prm)
+    r = oracle_run(phi, 20, prm=prm)
+    assert rel_l2(a["phi"], b["phi"]) <= 1e-6
+    assert rel_l2(a["f"], b["f"]) <= 1e-6
+    assert rel_l2(a["g"], b["g"]) <= 1e-6
+    assert rel_l2(a["phi"], r["phi"]) <= 1e-5
+
+
 def test_generic_and_fused_agree(ld):
     nz, ny, nx = 8, 16, 64
     phi = inputs.spinodal_phi(nx, ny, nz, seed=12, amplitude=0.4)
