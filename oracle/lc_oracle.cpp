@@ -4,8 +4,8 @@
 // chemical stress.
 //
 // TEST INFRASTRUCTURE ONLY. Nothing in the product path may link, load or call
-// this file: only the tests do. It shares no code, header, table or helper
-// with the CUDA library.
+// this file: only the tests and the smoke check (__graft_entry__.smoke) do.
+// It shares no code, header, table or helper with the CUDA library.
 //
 // What it computes. The paper's Ludwig test case is a liquid crystal: a
 // symmetric traceless 3x3 order-parameter tensor Q advected and relaxed by
