@@ -473,6 +473,27 @@ def cpu_baseline(sample_edge=96, sample_steps=20):
                       f"(C++ -O2, OpenMP over z-planes), {dt:.2f} s"}
 
 
+def lc_cpu_baseline(sample_edge=48, sample_steps=3):
+    """The liquid-crystal FP64 oracle, as it stands (one host core: it has no
+    threading), on a bounded sample of the bench's liquid-crystal workload: a
+    sample_edge^3 lattice from the same disordered Q, sample_steps steps."""
+    import oracle
+    from paper_1609_01479_gb300 import inputs
+
+    oracle.build()
+    n = sample_edge
+    prm = oracle.lc_param_vector()
+    q = inputs.random_q(n, n, n, seed=SEED)
+    f = oracle.lc_init((n, n, n), prm, rho=np.ones((n, n, n)), u=np.zeros((3, n, n, n)))
+    f, q = oracle.lc_step(f, q, prm, 1)  # warm-up
+    t0 = time.perf_counter()
+    oracle.lc_step(f, q, prm, sample_steps)
+    dt = time.perf_counter() - t0
+    return {"value": n ** 3 * sample_steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{n}^3 lattice of the liquid-crystal workload, {sample_steps} steps, FP64 oracle "
+                      f"(C++ -O2, one thread), {dt:.2f} s"}
+
+
 # --------------------------------------------------------------------------
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -617,6 +638,8 @@ def main():
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline()
+    if lc and not args.no_cpu_baseline and world == 1:
+        lc["cpu_baseline"] = lc_cpu_baseline()
     cfg = config_of(args)
     cfg["bytes_per_site_algorithmic"] = P["bytes_per_site"]
     cfg["precision"] = primary
