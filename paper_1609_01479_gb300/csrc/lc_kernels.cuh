@@ -12,11 +12,17 @@
 //   Q(t+1) = Q + Gamma H + S(W, Q) - u.grad(Q) (first-order upwind), W_ab = d_b u_a,
 //   S = (xi D + Om)(Q + I/3) + (Q + I/3)(xi D - Om) - 2 xi (Q + I/3) tr(Q W).
 // d is the 2-point central difference, lap the 7-point Laplacian, dt = 1.
-// Three launches per step, one thread per site in site order:
-//   k_lc_field    Q (+ its six neighbours) -> H (5 values), sigma (9)
-//   k_lc_collide  sigma (+ neighbours), f -> F, u (3 values stored), f collided
-//                 and pushed into the other buffer
-//   k_lc_update   Q, H, u (+ neighbours) -> Q of the next step (other buffer)
+// Two step forms (lc_ctx::kernel):
+//   generic, three launches, one thread per site in site order (any lattice):
+//     k_lc_field    Q (+ its six neighbours) -> H (5 values), sigma (9)
+//     k_lc_collide  sigma (+ neighbours), f -> F, u (3 values stored), f
+//                   collided and pushed into the other buffer
+//     k_lc_update   Q, H, u (+ neighbours) -> Q of the next step (other buffer)
+//   fused, two launches (nx % 32 == 0, ny % 8 == 0): k_lc_fused marches tile
+//     columns up z with Q and sigma in shared memory and writes only f and u;
+//     k_lc_update then recomputes H from Q (see the comment at k_lc_fused).
+// Every form uses the same per-site helpers in the same order, so FP64 gives
+// the same bits either way.
 // Q is stored as its five independent components (xx, xy, xz, yy, yz; zz =
 // -xx - yy): symmetric and traceless by construction (the trace of S, from
 // the lattice fluid's slight compressibility, is dropped).
