@@ -1,7 +1,7 @@
 """Checks at the benchmark's full size and in its launch configuration.
 
-Sub-box parity at 384^3 (the spinodal benchmark lattice, fused kernel, FP32
-and FP16-deviation storage) and at 512 x 512 x 448 (large enough for the
+Sub-box parity at 384^3 (the spinodal benchmark lattice, fused kernel, FP32,
+FP16-deviation and BF16-deviation storage) and at 512 x 512 x 448 (large enough for the
 kernels' 64-bit offsets): after n steps the macroscopic fields at a site
 depend only on the initial state within L-infinity distance 3n + 2 of it
 (each step reads phi within 2 sites for mu and grad mu, and propagation moves
@@ -108,10 +108,11 @@ def _subbox_parity(ld, nx, ny, nz, centres, seed, kernel="auto", precision="fp32
     sim.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16dev"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
 def test_subbox_parity_384cube(ld, precision):
     """The benchmark lattice and kernel, 10 steps, four 24^3 cubes (one on
-    the lattice's corner, so every periodic seam is inside a compared cube)."""
+    the lattice's corner, so every periodic seam is inside a compared cube).
+    BF16-dev runs the pair kernel's psi pass on four-site quads."""
     n = 384
     rng = np.random.default_rng(99)
     centres = [(0, 0, 0), (191, 7, 383)] + [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(2)]
