@@ -229,7 +229,7 @@ def test_trt_refusals(ld):
     sim.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16dev"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
 @pytest.mark.parametrize("stencil", [7, 19])
 def test_staged_and_register_fused_kernels_agree(ld, precision, stencil):
     """The staged kernel runs the register kernel's arithmetic on the same
@@ -240,7 +240,7 @@ def test_staged_and_register_fused_kernels_agree(ld, precision, stencil):
     prm = oracle.param_vector(stencil=stencil)
     a = gpu_run(ld, phi, 15, precision=precision, kernel="fused", prm=prm)
     b = gpu_run(ld, phi, 15, precision=precision, kernel="fused_staged", prm=prm)
-    same = {"fp32": 1e-6, "fp16dev": 2e-3}[precision]
+    same = {"fp32": 1e-6, "fp16dev": 2e-3, "bf16dev": 2e-2}[precision]
     assert rel_l2(b["phi"], a["phi"]) <= same
     assert rel_l2(b["f"], a["f"]) <= same
     assert rel_l2(b["g"], a["g"]) <= same
