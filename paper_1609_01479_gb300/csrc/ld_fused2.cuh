@@ -179,12 +179,12 @@ constexpr int pair_ctas_per_sm() {
     return TY == 8 ? 4 : 2;
 }
 
-template <int P, class I, bool ISO, int TY>
+template <int P, class I, bool ISO, int TY, bool SR = false>
 __global__ void __launch_bounds__(16 * TY, pair_ctas_per_sm<TY>())
     k_step_fused2(Geom g, Model<float> m, int nchunks, const typename Prec<P>::store_t* __restrict__ fs,
                   const typename Prec<P>::store_t* __restrict__ gs, typename Prec<P>::store_t* __restrict__ fd,
                   typename Prec<P>::store_t* __restrict__ gd, const float* __restrict__ ref_g,
-                  float* __restrict__ phi_out, float* __restrict__ mu_out, int* __restrict__ status) {
+                  float* __restrict__ phi_out, float* __restrict__ mu_out, SrStream sr, int* __restrict__ status) {
     using S = typename Prec<P>::store_t;
     static_assert(sizeof(S) == 2, "16-bit deviation forms");
     constexpr int TX = kTX, NT = 16 * TY;
@@ -359,16 +359,47 @@ __global__ void __launch_bounds__(16 * TY, pair_ctas_per_sm<TY>())
             const int ox = cx(i) > 0 ? (e == 0 ? 1 : oxp1) : (cx(i) < 0 ? (e == 0 ? oxm0 : -1) : 0);
             return s + e + ox + (cy(i) > 0 ? oyp : (cy(i) < 0 ? oym : 0)) + (cz(i) > 0 ? ozp : (cz(i) < 0 ? ozm : 0));
         };
-        // store the pair's values of direction i (paired when c_x = 0)
-        auto store = [&](S* base, int i, float2 v) {
+        // SR: the random 16 bits of (site, distribution a, direction i) are
+        // those sr_key gives (one splitmix64 word per four directions, from
+        // the site's stream position); the collisions hand the directions over
+        // as 1..18 and then 0, so each site keeps its current word and the
+        // group it belongs to.
+        unsigned long long srw[2] = {0ull, 0ull};
+        int srg[2] = {-1, -1};
+        auto sr_bits = [&](int e, int a, int i) -> unsigned {
+            const int grp = 5 * a + (i >> 2);
+            if (srg[e] != grp) {
+                const unsigned long long st = sr.base + (unsigned long long)(s + e) * kSrGamma;
+                srw[e] = sr_mix(st + (unsigned long long)grp * sr.stride);
+                srg[e] = grp;
+            }
+            return (unsigned)(srw[e] >> (16 * (i & 3))) & 0xffffu;
+        };
+        auto bits_of = [](S h) -> unsigned {
+            unsigned short u;
+            memcpy(&u, &h, 2);
+            return u;
+        };
+        // store the pair's values of distribution a, direction i (paired when c_x = 0)
+        auto store = [&](S* base, int a, int i, float2 v) {
+            S lo, hi;
+            if constexpr (SR) {
+                lo = Prec<P>::encode_sr(v.x, 0.0f, sr_bits(0, a, i));
+                hi = Prec<P>::encode_sr(v.y, 0.0f, sr_bits(1, a, i));
+            }
             if (cx(i) == 0) {
                 const int d = dest(i, 0);  // even; site 1 goes to d + 1
+                const unsigned packed = SR ? (bits_of(lo) | (bits_of(hi) << 16)) : pack2<P>(v);
                 if (site_ok(d, g.n, status) && site_ok(d + 1, g.n, status))
-                    __stcs(reinterpret_cast<unsigned*>(base + i * npad + d), pack2<P>(v));
+                    __stcs(reinterpret_cast<unsigned*>(base + i * npad + d), packed);
             } else {
+                if constexpr (!SR) {
+                    lo = Prec<P>::encode(v.x, 0.0f);
+                    hi = Prec<P>::encode(v.y, 0.0f);
+                }
                 const int d0 = dest(i, 0), d1 = dest(i, 1);
-                if (site_ok(d0, g.n, status)) __stcs(base + i * npad + d0, Prec<P>::encode(v.x, 0.0f));
-                if (site_ok(d1, g.n, status)) __stcs(base + i * npad + d1, Prec<P>::encode(v.y, 0.0f));
+                if (site_ok(d0, g.n, status)) __stcs(base + i * npad + d0, lo);
+                if (site_ok(d1, g.n, status)) __stcs(base + i * npad + d1, hi);
             }
         };
 
@@ -386,10 +417,10 @@ __global__ void __launch_bounds__(16 * TY, pair_ctas_per_sm<TY>())
         const float2 ux = mul2(fma2(f2(0.5f), Fx, jx), inv);
         const float2 uy = mul2(fma2(f2(0.5f), Fy, jy), inv);
         const float2 uz = mul2(fma2(f2(0.5f), Fz, jz), inv);
-        collide_f_dev2([&](int i) { return unpack2<P>(fpre[i]); }, [&](int i, float2 v) { store(fd, i, v); }, delta,
+        collide_f_dev2([&](int i) { return unpack2<P>(fpre[i]); }, [&](int i, float2 v) { store(fd, 0, i, v); }, delta,
                        rho, ux, uy, uz, Fx, Fy, Fz, m, dref);
         const unsigned* gt = reinterpret_cast<const unsigned*>(gring + (size_t)ps(k) * Q * (TY * TX) + ty * TX + tx);
-        collide_g_dev2([&](int i) { return unpack2<P>(gt[i * (TY * TX / 2)]); }, [&](int i, float2 v) { store(gd, i, v); },
+        collide_g_dev2([&](int i) { return unpack2<P>(gt[i * (TY * TX / 2)]); }, [&](int i, float2 v) { store(gd, 1, i, v); },
                        psi, ph, sub2(muc, f2(dref.muP)), ux, uy, uz, m, dref);
     }
 }
@@ -400,26 +431,32 @@ __global__ void __launch_bounds__(16 * TY, pair_ctas_per_sm<TY>())
 constexpr bool kPairs16 = true;
 constexpr int kPairRows = 8;
 
-template <int P, class I, bool ISO, int TY>
+template <int P, class I, bool ISO, int TY, bool SR>
 cudaError_t launch_fused2(ld_ctx* c, const void* src, void* dst, void* fields) {
     using S = typename Prec<P>::store_t;
     constexpr size_t kRingBytes = 3 * (size_t)Q * TY * kTX * sizeof(S);
-    cudaError_t e = set_max_dynamic_smem_once<k_step_fused2<P, I, ISO, TY>>((int)kRingBytes);
+    cudaError_t e = set_max_dynamic_smem_once<k_step_fused2<P, I, ISO, TY, SR>>((int)kRingBytes);
     if (e != cudaSuccess) return e;
     const Geom g{c->geom.nx, c->geom.ny, c->geom.nz, c->geom.n, c->geom.npad};
     const int nchunks = choose_chunks(g.nx, g.ny, g.nz, TY, c->num_sms, pair_ctas_per_sm<TY>());
     const dim3 grid(g.nx / kTX, g.ny / TY, nchunks);
-    k_step_fused2<P, I, ISO, TY><<<grid, 16 * TY, kRingBytes, c->stream>>>(
+    k_step_fused2<P, I, ISO, TY, SR><<<grid, 16 * TY, kRingBytes, c->stream>>>(
         g, model_of<float>(c->prm), nchunks, (const S*)f_part(c, src), (const S*)g_part(c, src), (S*)f_part(c, dst),
         (S*)g_part(c, dst), c->ref, fields ? (float*)fields : nullptr, fields ? (float*)fields + c->geom.npad : nullptr,
-        c->status);
+        sr_stream(c->prm.seed, c->sr_step, c->geom.n), c->status);
     return cudaGetLastError();
 }
 
 template <int P, class I, bool ISO>
 cudaError_t launch_fused2_rows(ld_ctx* c, const void* src, void* dst, void* fields) {
-    if (kPairRows == 16 && c->geom.ny % 16 == 0) return launch_fused2<P, I, ISO, 16>(c, src, dst, fields);
-    return launch_fused2<P, I, ISO, 8>(c, src, dst, fields);
+    const bool sr = c->prm.rounding == LD_ROUND_STOCHASTIC;
+    if constexpr (kPairRows == 16) {
+        if (c->geom.ny % 16 == 0)
+            return sr ? launch_fused2<P, I, ISO, 16, true>(c, src, dst, fields)
+                      : launch_fused2<P, I, ISO, 16, false>(c, src, dst, fields);
+    }
+    return sr ? launch_fused2<P, I, ISO, 8, true>(c, src, dst, fields)
+              : launch_fused2<P, I, ISO, 8, false>(c, src, dst, fields);
 }
 
 template <int P>

@@ -31,8 +31,8 @@ cudaError_t totals(ld_ctx* c, double* t) { LD_LP_DISPATCH(totals_p, c, t); }
 cudaError_t decode(ld_ctx* c, double* f, double* g) { LD_LP_DISPATCH(decode_p, c, f, g); }
 cudaError_t encode(ld_ctx* c, const double* f, const double* g) { LD_LP_DISPATCH(encode_p, c, f, g); }
 cudaError_t step_fused_regs(ld_ctx* c, const void* src, void* dst, void* fields) {
-    // the 16-bit forms, rounding to nearest: two sites per thread, packed FP32
-    if (kPairs16 && c->prm.rounding == LD_ROUND_NEAREST) {
+    // the 16-bit forms (either rounding): two sites per thread, packed FP32
+    if (kPairs16) {
         if (c->prec == LD_FP16DEV) return step_fused2_p<LD_FP16DEV>(c, src, dst, fields);
         if (c->prec == LD_BF16DEV) return step_fused2_p<LD_BF16DEV>(c, src, dst, fields);
     }
